@@ -1,0 +1,416 @@
+"""Benchmark of the pass-efficient randomized low-rank SVD on one GB300 (or N replicas).
+
+Workload (the configuration the headline metric -- "sketch-pass GB/s vs HBM
+peak; rank-k SVD time BF16 vs FP32 at equal error" -- is quoted on): block
+Krylov (Alg. 9 of Bjarkason 2018) with v = 4 views of a 65536 x 16384 matrix
+stored in BF16, A = U diag(j^-1.5) V^T with Haar U, V (synthetic, seeded),
+target rank k = 100, oversampling p = 20.  One step is one complete
+factorisation: four views of A on the tensor cores, block CholeskyQR2 after
+each inner view, the Krylov-basis QR, the core SVD and the lift.  The same
+matrix widened to FP32 runs the FP32 form of the identical schedule for the
+BF16-versus-FP32 comparison at equal error.
+
+value = bytes of A streamed by the step's views (4 x 2 GiB) / step time.
+A (2 GiB) is larger than L2 (129 MB), so every view reads it from HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun with N > 1 every rank runs the same workload on its own GPU
+(replicas: the method has no cross-GPU exchange on one matrix per GPU) and
+rank 0 reports the aggregate over ranks with max-over-ranks timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+M, N, K_RANK, P_OVER, VIEWS = 65536, 16384, 100, 20, 4
+METRIC = "sketch-pass GB/s (A bytes streamed by the views per factorisation / time)"
+WORKLOAD = "block_krylov_v4_bf16_65536x16384_k100_p20"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            backend = os.environ.get("BENCH_BACKEND", "nccl")
+            dist.init_process_group(backend=backend)
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(dist, value: float, device=None) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------- inputs
+def make_inputs(device):
+    """Seeded synthetic A (BF16, 65536 x 16384) and Omega (16384 x 120)."""
+    import torch
+
+    from paper_1804_07531_gb300 import synth
+    cfg = synth.CONFIGS["krylov_65536x16384_v4"]
+    r = N
+    u = synth.haar_torch(M, r, cfg["seed_u"], device=device)
+    v = synth.haar_torch(N, r, cfg["seed_v"], device=device)
+    sig = torch.tensor(synth.sigma_config("pow15", r), dtype=torch.float32, device=device)
+    a = torch.empty(M, N, dtype=torch.bfloat16, device=device)
+    prev_tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for i0 in range(0, M, 8192):
+        a[i0:i0 + 8192] = ((u[i0:i0 + 8192] * sig[None, :]) @ v.t()).bfloat16()
+    torch.backends.cuda.matmul.allow_tf32 = prev_tf32
+    del u, v
+    gen = torch.Generator(device=device)
+    gen.manual_seed(cfg["seed_omega"])
+    omega = torch.randn(N, K_RANK + P_OVER, generator=gen, device=device)
+    torch.cuda.synchronize()
+    return a, omega
+
+
+def recon_error(a, u, s, v):
+    """|A - U diag(s) V^T|_F in FP64 on the device (chunked, test metric only)."""
+    import torch
+    tot = 0.0
+    vt = (v.double() * s.double()[None, :]).t()
+    for i0 in range(0, a.shape[0], 4096):
+        blk = a[i0:i0 + 4096].double() - u[i0:i0 + 4096].double() @ vt
+        tot += float((blk * blk).sum())
+    return math.sqrt(tot)
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, "fallback"
+
+
+# --------------------------------------------------------- CPU baseline
+CPU_ROWS = 1024
+
+
+def cpu_sample():
+    """A row sample of the workload's matrix family for the FP64 oracle: the
+    same n = 16384 and spectrum law (sigma_j = j^-1.5, Haar factors), 1024
+    rows instead of 65536, and the same Omega shape."""
+    from paper_1804_07531_gb300 import synth
+    a = synth.usv(CPU_ROWS, N, synth.sigma_config("pow15", CPU_ROWS), 101, 102)
+    om = synth.gaussian(N, K_RANK + P_OVER, seed=103)
+    return a, om
+
+
+def _threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max(i.get("num_threads", 1) for i in threadpool_info())
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_time_one(a, om):
+    """Seconds for one FP64 oracle factorisation (Alg. 9, v = 4) of the sample."""
+    from oracle import algorithms as Al
+    t0 = time.perf_counter()
+    Al.block_krylov(a, om, K_RANK, VIEWS)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s: float = 10.0):
+    """The FP64 oracle's block Krylov on the row sample, scaled to the metric:
+    A bytes (BF16 element size, as in the workload) streamed by the 4 views
+    per second."""
+    a, om = cpu_sample()
+    runs, el = 0, 0.0
+    while runs < 1 or (el < budget_s and runs < 3):
+        el += cpu_time_one(a, om)
+        runs += 1
+    per = el / runs
+    return {
+        "value": VIEWS * CPU_ROWS * N * 2 / per / 1e9, "unit": "GB/s", "cores": _threads(), "kind": "oracle",
+        "sample": f"FP64 oracle Alg. 9 (v=4, k=100, p=20) on a {CPU_ROWS} x {N} row sample of the same "
+                  f"matrix family, {runs} run(s), {per:.2f} s each; bytes counted at BF16 size",
+    }
+
+
+# ------------------------------------------------------------ main arm
+def run_ours(args):
+    import torch
+
+    from paper_1804_07531_gb300 import api
+    from paper_1804_07531_gb300._binding import Handle
+
+    dist, rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    a, omega = make_inputs(dev)
+    h = Handle.get(local)
+    a_bytes = a.numel() * a.element_size()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return api.block_krylov(a, K_RANK, P_OVER, VIEWS, omega)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = api.device_status(local)
+    if st != 0:
+        raise RuntimeError(f"device status {st} after warm-up")
+
+    # ---- timed region (device events on the launching stream)
+    h.set_trace(True)
+    h.trace_read("view_range", reset=True)
+    launches0 = h.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        _barrier(dist)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            u, s, v = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        _barrier(dist)
+    launches = h.kernel_launches() - launches0
+    ms_step = e0.elapsed_time(e1) / args.steps
+    rng_ms, rng_n = h.trace_read("view_range")
+    cor_ms, cor_n = h.trace_read("view_corange")
+    orth_ms, orth_n = h.trace_read("orth")
+    svd_ms, svd_n = h.trace_read("core_svd", reset=True)
+    h.set_trace(False)
+    ms_max = _max_over_ranks(dist, ms_step, dev)
+    total_bytes = _sum_over_ranks(dist, VIEWS * a_bytes * args.steps, dev)
+    value = total_bytes / (ms_max * args.steps * 1e-3) / 1e9
+
+    # ---- accuracy of the BF16 form, and the FP32 form at equal error
+    e_bf16 = recon_error(a, u, s, v)
+    a32 = a.float()
+    del a
+    torch.cuda.empty_cache()
+    for _ in range(1):
+        api.block_krylov(a32, K_RANK, P_OVER, VIEWS, omega)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fsteps = max(1, min(3, args.steps))
+    f0.record(stream)
+    for _ in range(fsteps):
+        u32, s32, v32 = api.block_krylov(a32, K_RANK, P_OVER, VIEWS, omega)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_fp32 = f0.elapsed_time(f1) / fsteps
+    e_fp32 = recon_error(a32, u32, s32, v32)
+    a = a32.bfloat16()
+    del a32
+    torch.cuda.empty_cache()
+
+    # ---- end to end: host-resident A and Omega, copies inside the timed region
+    a_host = a.cpu().pin_memory()
+    om_host = omega.cpu().pin_memory()
+    del a
+    torch.cuda.empty_cache()
+    a_dev = torch.empty(a_host.shape, dtype=a_host.dtype, device=dev)
+    om_dev = torch.empty(om_host.shape, dtype=om_host.dtype, device=dev)
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        a_dev.copy_(a_host, non_blocking=True)
+        om_dev.copy_(om_host, non_blocking=True)
+        uu, ss, vv = api.block_krylov(a_dev, K_RANK, P_OVER, VIEWS, om_dev)
+        return uu.cpu(), ss.cpu(), vv.cpu()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    _barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        out = e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    t_e2e = _max_over_ranks(dist, t_e2e, dev)
+    e2e_val = _sum_over_ranks(dist, VIEWS * a_bytes, dev) / t_e2e / 1e9
+    h2d = a_host.numel() * a_host.element_size() + om_host.numel() * 4
+    d2h = sum(t.numel() * t.element_size() for t in out)
+
+    if rank != 0:
+        return
+    hbm, bf16_pk, src = _peaks()
+    view_launch_ms = (rng_ms + cor_ms) / max(1, rng_n + cor_n)
+    # algorithmic bytes of one view launch: A once + the thin operand (BF16) + the FP32 output
+    ell_avg = (3 * (K_RANK + P_OVER) + 2 * (K_RANK + P_OVER)) / 4.0
+    alg_bytes = a_bytes + (M + N) * ell_avg * (2 + 4) / 2
+    achieved = alg_bytes / (view_launch_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16",
+        "data": "synthetic (seeded Haar U, V; sigma_j = j^-1.5), A 2 GiB > L2 so every view reads HBM",
+        "config": {
+            "workload": WORKLOAD, "m": M, "n": N, "k": K_RANK, "p": P_OVER, "views": VIEWS,
+            "a_dtype": "bf16", "l2": "inputs larger than L2 (no flush needed)",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+        },
+        "roofline": {
+            "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(achieved / hbm, 4), "traffic": None,
+            "kernel": "view_bf16_kernel (range + co-range views)",
+            "launches_timed": rng_n + cor_n, "avg_launch_ms": round(view_launch_ms, 4),
+            "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback 6.8 TB/s",
+        },
+        "breakdown_ms_per_step": {
+            "views": round((rng_ms + cor_ms) / args.steps, 4),
+            "orth": round(orth_ms / args.steps, 4),
+            "core_svd": round(svd_ms / args.steps, 4),
+        },
+        "fp32_form": {
+            "ms_per_step": round(ms_fp32, 3), "recon_error": e_fp32, "bf16_recon_error": e_bf16,
+            "bf16_over_fp32_error": e_bf16 / e_fp32, "bf16_speedup": ms_fp32 / ms_max,
+        },
+        "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t_e2e * 1e3, 3)},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores, same metric and config:
+    each step is one oracle factorisation of the bounded row sample."""
+    dist, rank, world = _dist()
+    if rank != 0:
+        return
+    a, om = cpu_sample()
+    for _ in range(args.warmup):
+        cpu_time_one(a, om)
+    times = [cpu_time_one(a, om) for _ in range(args.steps)]
+    per = statistics.mean(times)
+    val = VIEWS * CPU_ROWS * N * 2 / per / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "m": M, "n": N, "k": K_RANK, "p": P_OVER,
+                                        "views": VIEWS},
+        "cpu_baseline": {"value": round(val, 4), "unit": "GB/s", "cores": _threads(), "kind": "oracle",
+                         "sample": f"FP64 oracle Alg. 9 (v=4) on a {CPU_ROWS} x {N} row sample, one "
+                                   f"factorisation per step; bytes counted at BF16 size"},
+        "e2e": {"value": round(val, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

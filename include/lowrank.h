@@ -1,0 +1,200 @@
+/*
+ * lowrank.h -- C ABI of liblowrank.so: pass-efficient randomized low-rank SVD
+ * on one GB300 GPU (sm_103a), after E. K. Bjarkason, "Pass-Efficient
+ * Randomized Algorithms for Low-Rank Matrix Approximation Using Any Number of
+ * Views" (2018).
+ *
+ * Notation.  The paper's target rank p, oversampling l and sketch width
+ * k = p + l are called k, p and ell = k + p here.  A is m x n (the paper's
+ * n_r x n_c).  Omega (n x ell) and Psi (m x ell2) are the caller's random
+ * test matrices (the paper's Omega_r and Omega_c); the library draws no random
+ * numbers.
+ *
+ * Conventions shared by every call.
+ *  - Memory.  Every lr_mat is a non-owning view of caller memory.  Unless a
+ *    call says otherwise, data points to device memory of the handle's device.
+ *    The library never allocates in a compute call: scratch comes from the
+ *    workspace given to lr_set_workspace (size from lr_workspace_size).
+ *  - Layout.  A is row-major (col_major = 0), ld = elements between rows,
+ *    ld >= cols, ld*elem_size a multiple of 16 bytes and data 16-byte
+ *    aligned (TMA).  Thin matrices (Omega, Psi, Y, Z, U, V) are column-major
+ *    FP32 (col_major = 1, ld >= rows).  S is a vector of k FP32 (or FP64)
+ *    values in a rows = k, cols = 1 view.  Small square factors (R) are FP64
+ *    column-major.
+ *  - Precision.  A in LR_F32 runs the FP32 form (FP32 operands, FP32
+ *    products); A in LR_BF16 runs the BF16 form (A and the thin operands in
+ *    BF16 on the tensor cores with FP32 accumulation).  Orthonormalisation,
+ *    small factorisations and outputs are FP32 with FP64-accumulated Grams.
+ *  - Streams.  stream is a cudaStream_t (NULL = legacy default stream).
+ *    Calls are asynchronous; outputs are valid once the stream has synced.
+ *    Argument errors are returned synchronously and nothing is launched.
+ *    Numerical failures found on the device (Cholesky breakdown, non-finite
+ *    values) and bounded-wait timeouts are recorded in a device status word
+ *    that lr_get_status reads (it synchronises the stream).
+ *  - Outputs.  S is sorted in descending order; U and V have orthonormal
+ *    columns; the sign of each pair (u_i, v_i) makes the largest-magnitude
+ *    entry of u_i positive.
+ *  - Threading.  A handle may be used by one host thread at a time.
+ */
+#ifndef LOWRANK_H
+#define LOWRANK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LR_OK = 0,
+  LR_ERR_INVALID_ARG = 1,  /* NULL pointer, k/p/v out of range           */
+  LR_ERR_SHAPE = 2,        /* inconsistent rows/cols/ld                   */
+  LR_ERR_DTYPE = 3,        /* unsupported element type or layout          */
+  LR_ERR_ALIGNMENT = 4,    /* pointer or stride not 16-byte aligned       */
+  LR_ERR_BREAKDOWN = 5,    /* Cholesky pivot <= 0 (sketch rank-deficient) */
+  LR_ERR_NONFINITE = 6,    /* NaN or Inf in a Gram matrix                 */
+  LR_ERR_TIMEOUT = 7,      /* a bounded device-side wait ran out          */
+  LR_ERR_CUDA = 8,         /* CUDA runtime error (see lr_last_error)      */
+  LR_ERR_NOMEM = 9,        /* workspace missing or too small              */
+  LR_ERR_UNSUPPORTED = 10  /* valid request this build does not serve     */
+} lr_status;
+
+typedef enum { LR_F32 = 0, LR_BF16 = 1, LR_F64 = 2 } lr_dtype;
+
+/* Non-owning matrix view. */
+typedef struct {
+  void* data;
+  int64_t rows, cols, ld;
+  int32_t dtype;     /* lr_dtype */
+  int32_t col_major; /* 1 column-major, 0 row-major */
+} lr_mat;
+
+/* Options; zero-initialise for defaults. */
+typedef struct {
+  int32_t l_c;              /* Alg. 7 truncation oversampling; < 0 means l_c = l_1 */
+  int32_t enhanced;         /* lr_block_krylov: 1 = row-streamed variant of Section 7.3 */
+  int32_t split_last;       /* BF16 form: last view's operand as BF16 hi + lo (two products) */
+  int32_t shifted_fallback; /* 1 = on Cholesky breakdown retry with a shifted Gram */
+  int32_t reserved[4];
+} lr_opts;
+
+typedef struct lr_handle_s* lr_handle;
+
+/* Handle on `device`.  Allocates a small device status word (the only
+ * allocation the library makes).  Errors: LR_ERR_INVALID_ARG, LR_ERR_CUDA. */
+lr_status lr_create(lr_handle* handle, int device);
+lr_status lr_destroy(lr_handle handle);
+
+/* Static description of a status code; never NULL. */
+const char* lr_status_string(lr_status status);
+/* Detail of the last error on this handle (empty string if none). */
+const char* lr_last_error(lr_handle handle);
+
+/* Workspace bytes sufficient for any call of this library on an m x n A with
+ * sketch widths ell1 (range) and ell2 (co-range, 0 if unused) and v views. */
+lr_status lr_workspace_size(lr_handle handle, int64_t m, int64_t n, int ell1, int ell2, int v,
+                            size_t* bytes);
+/* Device workspace owned by the caller, 256-byte aligned, kept until replaced. */
+lr_status lr_set_workspace(lr_handle handle, void* dev_ptr, size_t bytes);
+
+/* Synchronise `stream`, return the device status word (an lr_status) in
+ * *device_status and clear it. */
+lr_status lr_get_status(lr_handle handle, void* stream, int* device_status);
+
+/* One view of A (Section 4, Alg. 2 lines 4 and 6; Section 6.4, Alg. 7 line 3):
+ *   Y = A X   (X: n x ell1, Y: m x ell1) when X != NULL,
+ *   Z = A^T W (W: m x ell2, Z: n x ell2) when W != NULL.
+ * With both X and W the two products share one read of A from HBM (the
+ * paper's steps a) and b) of Alg. 7 done in parallel).  Y and Z are
+ * overwritten.  A is F32 or BF16 row-major; X, W, Y, Z are F32 column-major. */
+lr_status lr_sketch(lr_handle handle, const lr_mat* A, const lr_mat* X, const lr_mat* W,
+                    lr_mat* Y, lr_mat* Z, const lr_opts* opts, void* stream);
+
+/* Chained view (Section 6.7): Y = A X and Z = A^T Y from one read of A.
+ * Same argument rules as lr_sketch; Y and Z are overwritten. */
+lr_status lr_sketch_chained(lr_handle handle, const lr_mat* A, const lr_mat* X, lr_mat* Y,
+                            lr_mat* Z, const lr_opts* opts, void* stream);
+
+/* Thin QR in place, Y (m x ell, F32 column-major, m >= ell) -> Q with
+ * Y = Q R, Q^T Q = I, R upper triangular with positive diagonal (the qr of
+ * Section 2).  Computed by block CholeskyQR2: column blocks of width <= 128,
+ * each projected out of the previous ones twice (BCGS2) and factorised by
+ * CholeskyQR2 with FP64-accumulated Grams.  R (ell x ell, F64 column-major)
+ * may be NULL.  Rank-deficient Y raises LR_ERR_BREAKDOWN in the status word
+ * unless opts->shifted_fallback is set. */
+lr_status lr_orth(lr_handle handle, lr_mat* Y, lr_mat* R, const lr_opts* opts, void* stream);
+
+/* Generalized subspace iteration, Alg. 2 (Section 4): v >= 2 views, sketch
+ * width ell = k + p, Omega n x ell.  Outputs U (m x k), S (k), V (n x k). */
+lr_status lr_subspace_iter(lr_handle handle, const lr_mat* A, int k, int p, int v,
+                           const lr_mat* Omega, lr_mat* U, lr_mat* S, lr_mat* V,
+                           const lr_opts* opts, void* stream);
+
+/* Single-pass TSVD, Alg. 7 (Section 6.4, Tropp variant): Omega n x ell1,
+ * Psi m x ell2 with ell2 >= ell1 > k; opts->l_c in [0, ell1 - k] truncates
+ * Q_c to its leading k + l_c left singular vectors (l_c < 0: none, the
+ * baseline of Section 6.2).  Both sketches come from one read of A. */
+lr_status lr_single_pass(lr_handle handle, const lr_mat* A, int k, const lr_mat* Omega,
+                         const lr_mat* Psi, lr_mat* U, lr_mat* S, lr_mat* V,
+                         const lr_opts* opts, void* stream);
+
+/* Generalized block Krylov, Alg. 9 (Section 7.2), v >= 2 views.  With
+ * opts->enhanced = 1: the row-streamed variant of Section 7.3, in which each
+ * of the first v-1 views yields A X and A^T (A X) from one read of A, giving
+ * the co-range Krylov space of Alg. 9 with 2v-1 views. */
+lr_status lr_block_krylov(lr_handle handle, const lr_mat* A, int k, int p, int v,
+                          const lr_mat* Omega, lr_mat* U, lr_mat* S, lr_mat* V,
+                          const lr_opts* opts, void* stream);
+
+/* Row-streamed one-pass QB of Section 6.7: Y = A Omega and A^T Y from one
+ * read, Q_c R_c = Y, B^T = (A^T Y) R_c^{-1}, then the TSVD of B. */
+lr_status lr_rowwise_single_pass(lr_handle handle, const lr_mat* A, int k, const lr_mat* Omega,
+                                 lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts,
+                                 void* stream);
+
+/* Host-streamed single pass (Section 6.1 streaming model, A = sum of column
+ * panels): A_host is F32 row-major in pinned host memory; it is copied to the
+ * device in panels of panel_cols columns through two device panel buffers
+ * (carved from the workspace) on a copy stream overlapped with the sketches.
+ * Otherwise as lr_single_pass. */
+lr_status lr_single_pass_host(lr_handle handle, const lr_mat* A_host, int64_t panel_cols, int k,
+                              const lr_mat* Omega, const lr_mat* Psi, lr_mat* U, lr_mat* S,
+                              lr_mat* V, const lr_opts* opts, void* stream);
+
+/* Reverse pass of lr_subspace_iter for the loss L = sum_i dS_i sigma_i
+ * (dS: k weights, F32): writes dA = dL/dA (m x n, F32 row-major, same shape
+ * as A, overwritten).  The forward views are recomputed, not stored.  A must
+ * be F32. */
+lr_status lr_subspace_iter_backward(lr_handle handle, const lr_mat* A, int k, int p, int v,
+                                    const lr_mat* Omega, const lr_mat* dS, lr_mat* dA,
+                                    const lr_opts* opts, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Instrumentation (the paper has no counterpart; used by benchmarks).
+ * ------------------------------------------------------------------- */
+
+/* Kernel classes timed by the trace. */
+typedef enum {
+  LR_TRACE_VIEW_RANGE = 0,   /* Y = A X on the tensor cores (BF16) or SIMT (FP32) */
+  LR_TRACE_VIEW_CORANGE = 1, /* Z = A^T W                                          */
+  LR_TRACE_ORTH = 2,         /* one lr_orth-equivalent thin QR (all its kernels)    */
+  LR_TRACE_CORE_SVD = 3,     /* the small core SVD                                  */
+  LR_TRACE_COUNT = 4
+} lr_trace_kind;
+
+/* Turn per-launch CUDA-event timing of the classes above on (1) or off (0).
+ * Enabling pre-creates a pool of events (no allocation afterwards); each
+ * timed launch records two events on the call's stream. */
+lr_status lr_set_trace(lr_handle handle, int on);
+/* Synchronise the device, then return the accumulated device time (ms) and
+ * the number of timed launches of `kind` since tracing was enabled or last
+ * reset (reset != 0 clears the accumulators). */
+lr_status lr_trace_read(lr_handle handle, int kind, double* total_ms, int64_t* launches, int reset);
+/* Number of CUDA kernels this process has launched through the library. */
+lr_status lr_kernel_launches(lr_handle handle, uint64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOWRANK_H */

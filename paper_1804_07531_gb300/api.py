@@ -1,0 +1,158 @@
+"""Python API over liblowrank.so: the paper's algorithms on torch CUDA tensors.
+
+Names follow the C ABI (include/lowrank.h).  Every call takes A (m x n,
+row-major float32 or bfloat16, on a CUDA device) and the caller's random test
+matrices, runs on the current CUDA stream and returns new column-major
+float32 tensors.  Letters: k = target rank, p = oversampling, ell = k + p,
+v = number of views (the paper's p, l, p + l, v).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from ._binding import (Handle, LowrankError, LrMat, _opts, _stream, col_major, empty_cm, lib, mat_a,
+                       mat_thin)
+
+__all__ = [
+    "sketch", "sketch_chained", "orth", "subspace_iter", "single_pass", "block_krylov",
+    "rowwise_single_pass", "device_status", "LowrankError",
+]
+
+
+def _prep(a, *thin):
+    if not a.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    if a.stride(1) != 1:
+        a = a.contiguous()
+    return a, [None if t is None else col_major(t.to(device=a.device, dtype=torch.float32)) for t in thin]
+
+
+def _call(h, fn, *args):
+    h.check(fn(h.h, *args))
+
+
+def _p(m: LrMat):
+    return ctypes.byref(m)
+
+
+def sketch(a, x=None, w=None, stream=None):
+    """Y = A X and/or Z = A^T W (both from one read of A when both are given)."""
+    a, (x, w) = _prep(a, x, w)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    y = empty_cm(m, x.shape[1], a.device) if x is not None else None
+    z = empty_cm(n, w.shape[1], a.device) if w is not None else None
+    h.reserve(m, n, max(1, x.shape[1] if x is not None else 1), w.shape[1] if w is not None else 0)
+    mA = mat_a(a)
+    args = [_p(mA)]
+    keep = []
+    for t in (x, w, y, z):
+        if t is None:
+            args.append(None)
+        else:
+            mt = mat_thin(t)
+            keep.append(mt)
+            args.append(_p(mt))
+    o = _opts()
+    _call(h, lib().lr_sketch, *args, ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return y, z
+
+
+def sketch_chained(a, x, stream=None):
+    """Y = A X and Z = A^T Y from one read of A (Section 6.7)."""
+    a, (x,) = _prep(a, x)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    y = empty_cm(m, x.shape[1], a.device)
+    z = empty_cm(n, x.shape[1], a.device)
+    h.reserve(m, n, x.shape[1])
+    mA, mx, my, mz = mat_a(a), mat_thin(x), mat_thin(y), mat_thin(z)
+    o = _opts()
+    _call(h, lib().lr_sketch_chained, _p(mA), _p(mx), _p(my), _p(mz), ctypes.byref(o),
+          ctypes.c_void_p(_stream(stream)))
+    return y, z
+
+
+def orth(y, want_r=True, shifted_fallback=False, stream=None):
+    """Thin QR of y (rows >= cols) by block CholeskyQR2: returns (Q, R)."""
+    q = col_major(y.to(torch.float32)).clone() if y.stride(0) != 1 else y.to(torch.float32).clone()
+    q = col_major(q)
+    h = Handle.get(q.device)
+    rows, cols = q.shape
+    h.reserve(rows, cols, cols)
+    r = torch.zeros(cols, cols, dtype=torch.float64, device=q.device).t() if want_r else None
+    mq = mat_thin(q)
+    mr = mat_thin(r) if want_r else None
+    o = _opts(shifted_fallback=shifted_fallback)
+    _call(h, lib().lr_orth, _p(mq), _p(mr) if want_r else None, ctypes.byref(o),
+          ctypes.c_void_p(_stream(stream)))
+    return q, r
+
+
+def _outs(a, k):
+    m, n = a.shape
+    return empty_cm(m, k, a.device), torch.empty(k, dtype=torch.float32, device=a.device), empty_cm(n, k, a.device)
+
+
+def subspace_iter(a, k, p, v, omega, shifted_fallback=False, stream=None):
+    """Alg. 2: generalized subspace iteration with v >= 2 views -> (U, S, V)."""
+    a, (omega,) = _prep(a, omega)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    h.reserve(m, n, k + p, 0, v)
+    u, s, vv = _outs(a, k)
+    mats = [mat_a(a), mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts(shifted_fallback=shifted_fallback)
+    _call(h, lib().lr_subspace_iter, _p(mats[0]), k, p, v, _p(mats[1]), _p(mats[2]), _p(mats[3]),
+          _p(mats[4]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+def block_krylov(a, k, p, v, omega, enhanced=False, shifted_fallback=False, stream=None):
+    """Alg. 9 (or the row-streamed variant of Section 7.3 with enhanced=True)."""
+    a, (omega,) = _prep(a, omega)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    h.reserve(m, n, k + p, 0, v)
+    u, s, vv = _outs(a, k)
+    mats = [mat_a(a), mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts(enhanced=enhanced, shifted_fallback=shifted_fallback)
+    _call(h, lib().lr_block_krylov, _p(mats[0]), k, p, v, _p(mats[1]), _p(mats[2]), _p(mats[3]),
+          _p(mats[4]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+def rowwise_single_pass(a, k, omega, stream=None):
+    """Section 6.7: 2-view-accurate TSVD from one row-streamed read of A."""
+    a, (omega,) = _prep(a, omega)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    h.reserve(m, n, omega.shape[1])
+    u, s, vv = _outs(a, k)
+    mats = [mat_a(a), mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts()
+    _call(h, lib().lr_rowwise_single_pass, _p(mats[0]), k, _p(mats[1]), _p(mats[2]), _p(mats[3]),
+          _p(mats[4]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+def single_pass(a, k, omega, psi, l_c=None, stream=None):
+    """Alg. 7: 1-view TSVD (l_c=None: the baseline with l_c = l_1)."""
+    a, (omega, psi) = _prep(a, omega, psi)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    h.reserve(m, n, omega.shape[1], psi.shape[1], 1)
+    u, s, vv = _outs(a, k)
+    mats = [mat_a(a), mat_thin(omega), mat_thin(psi), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts(l_c=l_c)
+    _call(h, lib().lr_single_pass, _p(mats[0]), k, _p(mats[1]), _p(mats[2]), _p(mats[3]), _p(mats[4]),
+          _p(mats[5]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+def device_status(device=None, stream=None) -> int:
+    """Read and clear the device status word (synchronises the stream)."""
+    h = Handle.get(device if device is not None else torch.cuda.current_device())
+    return h.status(stream)

@@ -1,0 +1,883 @@
+// C ABI of liblowrank: argument validation, workspace arena and the drivers
+// of the paper's view schedules (Bjarkason 2018):
+//   lr_subspace_iter        Alg. 2 (generalized subspace iteration, any v >= 2)
+//   lr_single_pass          Alg. 7 (1-view, Tropp variant with l_c)
+//   lr_block_krylov         Alg. 9 (generalized block Krylov) and, with
+//                           opts->enhanced, the row-streamed variant of Sec. 7.3
+//   lr_rowwise_single_pass  the one-pass QB of Section 6.7
+// plus the building blocks lr_sketch / lr_sketch_chained (views) and lr_orth
+// (thin QR by block CholeskyQR2).  Every step runs in this library's kernels.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+struct lr_trace_rec {
+  int kind;
+  cudaEvent_t begin, end;
+};
+
+struct lr_handle_s {
+  int device = 0;
+  int* status_dev = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  std::string last_error;
+  // instrumentation: a fixed pool of events, filled in order while tracing
+  bool trace = false;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  std::vector<lr_trace_rec> recs;
+  double acc_ms[LR_TRACE_COUNT] = {};
+  int64_t acc_n[LR_TRACE_COUNT] = {};
+};
+
+namespace lr {
+std::atomic<uint64_t> g_kernel_launches{0};
+}
+
+namespace lr {
+namespace {
+
+// FP32 column-major thin matrix.
+struct Mat {
+  float* p = nullptr;
+  int64_t rows = 0, cols = 0, ld = 0;
+  float* col(int64_t c) const { return p + c * ld; }
+};
+
+struct Ctx {
+  lr_handle h = nullptr;
+  cudaStream_t s = nullptr;
+  Arena ar;
+  int sms = 1;
+  int* status = nullptr;
+  lr_opts opt{};
+  bool measure = false;
+};
+
+// Records a begin/end event pair around a traced region (no-op unless the
+// handle traces and events remain in the pool).
+struct TraceScope {
+  lr_handle h = nullptr;
+  cudaStream_t s = nullptr;
+  int kind = 0;
+  cudaEvent_t end = nullptr;
+  TraceScope(const Ctx& c, int k) {
+    if (c.measure || !c.h || !c.h->trace || c.h->pool_used + 2 > c.h->pool.size()) return;
+    h = c.h;
+    s = c.s;
+    kind = k;
+    cudaEvent_t b = h->pool[h->pool_used++];
+    end = h->pool[h->pool_used++];
+    cudaEventRecord(b, s);
+    h->recs.push_back({kind, b, end});
+  }
+  ~TraceScope() {
+    if (h) cudaEventRecord(end, s);
+  }
+};
+
+// A as the drivers see it.
+struct AMat {
+  const void* p = nullptr;
+  int64_t m = 0, n = 0, ld = 0;
+  bool bf16 = false;
+  const __nv_bfloat16* b() const { return static_cast<const __nv_bfloat16*>(p); }
+  const float* f() const { return static_cast<const float*>(p); }
+  size_t elem() const { return bf16 ? 2 : 4; }
+};
+
+constexpr int kMaxBlock = 128;  // column block width of block CholeskyQR2
+
+inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+// ----------------------------------------------------------- thin GEMMs
+// C (M x N) = alpha op(A) op(B) + beta C, all FP32 column-major.
+void gemm(Ctx& c, int64_t M, int64_t N, int64_t K, bool ta, const float* A, int64_t lda, bool tb, const float* B,
+          int64_t ldb, float* C, int64_t ldc, float alpha = 1.f, float beta = 0.f) {
+  if (c.measure) return;
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K; g.ta = ta; g.tb = tb; g.alpha = alpha; g.beta = beta;
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
+  g.mode = GEMM_STORE;
+  sgemm(g, c.s);
+}
+
+// C64 (M x N, ld ldc) = op(A)^T-style reduction over a long K with FP32
+// products and FP64 accumulation across K slices (Grams, cross-Grams).
+void gram64(Ctx& c, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+            double* C64, int64_t ldc) {
+  if (c.measure) return;
+  LR_CHECK_CUDA(cudaMemsetAsync(C64, 0, size_t(ldc) * N * sizeof(double), c.s));
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K; g.ta = true; g.tb = false;
+  g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C64 = C64; g.ldc = ldc;
+  g.mode = GEMM_ATOMIC_F64;
+  g.split_k = split_for(M, N, K, c.sms);
+  sgemm(g, c.s);
+}
+
+// -------------------------------------------------------------- views
+// out (rows_out x ell) = A[r0:r0+rows, :] B (mode 0, out = Y rows r0..) or
+// += A[r0:r0+rows, :]^T B[r0:r0+rows, :] (mode 1, out = Z).  The output must
+// be zeroed by the caller before the first contribution.
+void view_band(Ctx& c, const AMat& A, int mode, const float* B, int64_t ldb, int ell, float* out, int64_t ldo,
+               int64_t r0, int64_t rows, const __nv_bfloat16* Bb = nullptr, int64_t ldbb = 0) {
+  if (rows <= 0) return;
+  if (A.bf16) {
+    ArenaScope sc(c.ar);
+    const __nv_bfloat16* op = Bb;
+    int64_t ldop = ldbb;
+    const int64_t orows = (mode == 0) ? A.n : rows;
+    if (!op) {
+      ldop = round8(orows);
+      __nv_bfloat16* tmp = c.ar.take<__nv_bfloat16>(size_t(ldop) * ell);
+      if (!c.measure) f32_to_bf16(mode == 0 ? B : B + r0, ldb, tmp, nullptr, ldop, orows, ell, c.s);
+      op = tmp;
+    } else if (mode == 1) {
+      op = Bb + r0;
+    }
+    if (c.measure) return;
+    TraceScope tr(c, mode == 0 ? LR_TRACE_VIEW_RANGE : LR_TRACE_VIEW_CORANGE);
+    for (int g0 = 0; g0 < ell; g0 += 256) {
+      const int w = std::min(256, ell - g0);
+      ViewBf16Args a;
+      a.device = c.h->device;
+      a.mode = mode;
+      a.A = A.b();
+      a.lda = A.ld;
+      a.row0 = r0;
+      a.rows = rows;
+      a.n = A.n;
+      a.B = op + int64_t(g0) * ldop;
+      a.ldb = ldop;
+      a.ell = w;
+      a.out = (mode == 0 ? out + r0 : out) + int64_t(g0) * ldo;
+      a.ldo = ldo;
+      a.status = c.status;
+      view_bf16(a, c.s);
+    }
+  } else {
+    if (c.measure) return;
+    TraceScope tr(c, mode == 0 ? LR_TRACE_VIEW_RANGE : LR_TRACE_VIEW_CORANGE);
+    GemmArgs g;
+    g.mode = GEMM_ATOMIC_F32;
+    g.ldb = ldb;
+    g.ldc = ldo;
+    if (mode == 0) {
+      g.M = rows; g.N = ell; g.K = A.n; g.ta = true;
+      g.A = A.f() + r0 * A.ld; g.lda = A.ld;
+      g.B = B;
+      g.C = out + r0;
+    } else {
+      g.M = A.n; g.N = ell; g.K = rows; g.ta = false;
+      g.A = A.f() + r0 * A.ld; g.lda = A.ld;
+      g.B = B + r0;
+      g.C = out;
+    }
+    g.split_k = split_for(g.M, g.N, g.K, c.sms);
+    sgemm(g, c.s);
+  }
+}
+
+int64_t band_rows(const AMat& A) {
+  // about 48 MB of A per band so a band read by the range product is still
+  // in L2 (129 MB) when the co-range product reads it
+  int64_t r = int64_t(48) * 1024 * 1024 / (A.n * int64_t(A.elem()));
+  r = std::max<int64_t>(256, r / 256 * 256);
+  return std::min<int64_t>(r, (A.m + 255) / 256 * 256);
+}
+
+// Y = A X (X: n x ell).
+void view_range(Ctx& c, const AMat& A, const Mat& X, Mat Y) {
+  if (!c.measure) zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
+  view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, 0, A.m);
+}
+// Z = A^T W (W: m x ell).
+void view_corange(Ctx& c, const AMat& A, const Mat& W, Mat Z) {
+  if (!c.measure) zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
+  view_band(c, A, 1, W.p, W.ld, int(W.cols), Z.p, Z.ld, 0, A.m);
+}
+
+// Y = A X and Z = A^T W sharing each L2-sized band of A (Alg. 7 line 3).
+void view_dual(Ctx& c, const AMat& A, const Mat& X, Mat Y, const Mat& W, Mat Z) {
+  ArenaScope sc(c.ar);
+  const __nv_bfloat16 *xb = nullptr, *wb = nullptr;
+  int64_t ldx = 0, ldw = 0;
+  if (A.bf16) {
+    ldx = round8(A.n);
+    ldw = round8(A.m);
+    auto* tx = c.ar.take<__nv_bfloat16>(size_t(ldx) * X.cols);
+    auto* tw = c.ar.take<__nv_bfloat16>(size_t(ldw) * W.cols);
+    if (!c.measure) {
+      f32_to_bf16(X.p, X.ld, tx, nullptr, ldx, A.n, X.cols, c.s);
+      f32_to_bf16(W.p, W.ld, tw, nullptr, ldw, A.m, W.cols, c.s);
+    }
+    xb = tx;
+    wb = tw;
+  }
+  if (c.measure) return;
+  zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
+  zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
+  const int64_t rb = band_rows(A);
+  for (int64_t r0 = 0; r0 < A.m; r0 += rb) {
+    const int64_t rows = std::min(rb, A.m - r0);
+    view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, xb, ldx);
+    view_band(c, A, 1, W.p, W.ld, int(W.cols), Z.p, Z.ld, r0, rows, wb, ldw);
+  }
+}
+
+// Y = A X and Z = A^T Y, band by band (Section 6.7: each band of rows is used
+// for its slice of Y and, while it is still in L2, for its share of A^T Y).
+void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
+  ArenaScope sc(c.ar);
+  const __nv_bfloat16 *xb = nullptr;
+  __nv_bfloat16* yb = nullptr;
+  int64_t ldx = 0, ldyb = 0;
+  if (A.bf16) {
+    ldx = round8(A.n);
+    ldyb = round8(A.m);
+    auto* tx = c.ar.take<__nv_bfloat16>(size_t(ldx) * X.cols);
+    yb = c.ar.take<__nv_bfloat16>(size_t(ldyb) * Y.cols);
+    if (!c.measure) f32_to_bf16(X.p, X.ld, tx, nullptr, ldx, A.n, X.cols, c.s);
+    xb = tx;
+  }
+  if (c.measure) return;
+  zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
+  zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
+  const int64_t rb = band_rows(A);
+  for (int64_t r0 = 0; r0 < A.m; r0 += rb) {
+    const int64_t rows = std::min(rb, A.m - r0);
+    view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, xb, ldx);
+    if (A.bf16) f32_to_bf16(Y.p + r0, Y.ld, yb + r0, nullptr, ldyb, rows, Y.cols, c.s);
+    view_band(c, A, 1, Y.p, Y.ld, int(Y.cols), Z.p, Z.ld, r0, rows, yb, ldyb);
+  }
+}
+
+// ------------------------------------------------- block CholeskyQR2
+// In place thin QR of Y (m x L): column blocks of width <= 128; each block
+// is projected out of the previous ones twice (BCGS2, the second pass
+// restores the orthogonality lost in the first) and factorised by
+// CholeskyQR2 (Gram in FP32 products with FP64 accumulation, Cholesky and
+// triangular inverse in one CTA).  R (L x L FP64, ld L) receives the
+// triangular factor when non-null: off-diagonal blocks are the summed
+// projection coefficients, diagonal blocks R2 R1.
+void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
+  const int64_t m = Y.rows;
+  const int L = int(Y.cols);
+  LR_REQUIRE(m >= L, LR_ERR_SHAPE, "orth needs rows >= cols");
+  ArenaScope sc(c.ar);
+  const int nb = (L + kMaxBlock - 1) / kMaxBlock;
+  const int wmax = (L + nb - 1) / nb;
+  float* T = c.ar.take<float>(size_t(m) * wmax);
+  double* G64 = c.ar.take<double>(size_t(std::max(L, wmax)) * wmax);
+  float* C32 = c.ar.take<float>(size_t(L) * wmax);
+  float* Rinv = c.ar.take<float>(size_t(wmax) * wmax);
+  if (c.measure) return;
+  TraceScope tr(c, LR_TRACE_ORTH);
+  if (R) LR_CHECK_CUDA(cudaMemsetAsync(R, 0, size_t(L) * L * sizeof(double), c.s));
+  // Shifted CholeskyQR3 (Fukaya et al. 2020): with FP32 Cholesky, plain
+  // CholeskyQR2 breaks down once kappa(Y) nears 1e3, which sketches of
+  // steep spectra and Krylov bases reach, so every block takes one shifted
+  // pass followed by two unshifted ones.  `robust` is kept for callers that
+  // know their input is ill-conditioned; it no longer changes the passes.
+  (void)robust;
+  const bool shifted = true;
+  const int passes = 3;
+  int c0 = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int w = L / nb + (b < L % nb ? 1 : 0);
+    float* Yb = Y.col(c0);
+    if (c0 > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        gram64(c, c0, w, m, Y.p, Y.ld, Yb, Y.ld, G64, c0);          // C = Q_prev^T Y_b
+        f64_to_f32(G64, c0, C32, c0, c0, w, c.s);
+        gemm(c, m, w, c0, false, Y.p, Y.ld, false, C32, c0, Yb, Y.ld, -1.f, 1.f);  // Y_b -= Q_prev C
+        if (R) add_block_f64(R, L, 0, c0, G64, c0, c0, w, c.s);
+      }
+    }
+    // CholeskyQR passes ping-pong between Y_b and T; R_bb = R_last ... R_1.
+    bool in_t = false;
+    for (int pass = 0; pass < passes; ++pass) {
+      float* src = in_t ? T : Yb;
+      float* dst = in_t ? Yb : T;
+      const int64_t lds = in_t ? m : Y.ld, ldd = in_t ? Y.ld : m;
+      gram64(c, w, w, m, src, lds, src, lds, G64, w);
+      chol_inv(G64, w, Rinv, w, R ? R + c0 + int64_t(c0) * L : nullptr, L, pass == 0,
+               (shifted && pass == 0) ? 1 : 0, c.status, c.s);
+      gemm(c, m, w, w, false, src, lds, false, Rinv, w, dst, ldd);
+      in_t = !in_t;
+    }
+    if (in_t) copy_f32(T, m, Yb, Y.ld, m, w, c.s);
+    c0 += w;
+  }
+}
+
+// --------------------------------------------------------- core SVD
+// R (n x n upper, FP64) = W diag(S) Vj^T, all outputs FP32 n x n.
+void core_svd(Ctx& c, const double* R, int n, float* W, float* Vj, float* S) {
+  ArenaScope sc(c.ar);
+  float* M = c.ar.take<float>(size_t(n) * n);
+  if (c.measure) return;
+  TraceScope tr(c, LR_TRACE_CORE_SVD);
+  r_to_f32(R, n, n, M, n, false, c.s);
+  jacobi_svd(M, n, n, n, W, n, Vj, n, S, nullptr, c.status, c.s);
+}
+
+struct Outs {
+  Mat U, V;
+  void* S = nullptr;
+};
+
+void write_outputs(Ctx& c, const Mat& Qleft, const float* Lsel, const Mat& Qright, const float* Rsel, int Lk,
+                   const float* Sv, int k, Outs& o) {
+  if (c.measure) return;
+  gemm(c, o.U.rows, k, Lk, false, Qleft.p, Qleft.ld, false, Lsel, Lk, o.U.p, o.U.ld);
+  gemm(c, o.V.rows, k, Lk, false, Qright.p, Qright.ld, false, Rsel, Lk, o.V.p, o.V.ld);
+  fix_signs(o.U.p, o.U.ld, o.U.rows, o.V.p, o.V.ld, o.V.rows, k, c.s);
+  LR_CHECK_CUDA(cudaMemcpyAsync(o.S, Sv, sizeof(float) * k, cudaMemcpyDeviceToDevice, c.s));
+}
+
+// ------------------------------------------------------------ Alg. 2
+void run_subspace(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o) {
+  ArenaScope sc(c.ar);
+  Mat Qc{c.ar.take<float>(size_t(A.m) * ell), A.m, ell, A.m};
+  Mat Qr{c.ar.take<float>(size_t(A.n) * ell), A.n, ell, A.n};
+  double* Rc = c.ar.take<double>(size_t(ell) * ell);
+  double* Rr = c.ar.take<double>(size_t(ell) * ell);
+  float* W = c.ar.take<float>(size_t(ell) * ell);
+  float* Vj = c.ar.take<float>(size_t(ell) * ell);
+  float* Sv = c.ar.take<float>(size_t(ell));
+  Mat cur = Om;  // Q_r = Omega (Alg. 2 line 1: the raw Gaussian)
+  for (int j = 1; j <= v; ++j) {
+    if (j % 2 == 1) {
+      view_range(c, A, cur, Qc);       // A Q_r
+      orth(c, Qc, Rc);                 // [Q_c, R_c] = qr(A Q_r)
+    } else {
+      view_corange(c, A, Qc, Qr);      // A^T Q_c
+      orth(c, Qr, Rr);                 // [Q_r, R_r] = qr(A^T Q_c)
+      cur = Qr;
+    }
+  }
+  if (v % 2 == 0) {
+    // R_r = V^ L U^T: left vectors of R_r give V, right vectors give U.
+    core_svd(c, Rr, ell, W, Vj, Sv);
+    write_outputs(c, Qc, Vj, Qr, W, ell, Sv, k, o);
+  } else {
+    // R_c = U^ L V^T
+    core_svd(c, Rc, ell, W, Vj, Sv);
+    write_outputs(c, Qc, W, Qr, Vj, ell, Sv, k, o);
+  }
+}
+
+// ------------------------------------------------------------ Alg. 9
+void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o) {
+  ArenaScope sc(c.ar);
+  const bool even = v % 2 == 0;
+  const int nb = even ? v / 2 : (v - 1) / 2;
+  const int Lk = nb * ell;
+  const int64_t kdim = even ? A.m : A.n, odim = even ? A.n : A.m;
+  Mat K{c.ar.take<float>(size_t(kdim) * Lk), kdim, Lk, kdim};
+  Mat Tb{c.ar.take<float>(size_t(odim) * ell), odim, ell, odim};
+  Mat F{c.ar.take<float>(size_t(odim) * Lk), odim, Lk, odim};  // final view
+  double* Rf = c.ar.take<double>(size_t(Lk) * Lk);
+  float* W = c.ar.take<float>(size_t(Lk) * Lk);
+  float* Vj = c.ar.take<float>(size_t(Lk) * Lk);
+  float* Sv = c.ar.take<float>(size_t(Lk));
+  Mat prev = Om;
+  int blk = 0;
+  for (int j = 1; j <= v - 1; ++j) {
+    const bool odd = j % 2 == 1;
+    const bool in_k = odd == even;
+    Mat out = in_k ? Mat{K.col(int64_t(blk) * ell), kdim, ell, kdim} : Tb;
+    if (odd) view_range(c, A, prev, out);
+    else view_corange(c, A, prev, out);
+    if (j < v - 1) orth(c, out, nullptr);
+    if (in_k) ++blk;
+    prev = out;
+  }
+  orth(c, K, nullptr, true);             // Q = qr(K)
+  if (even) {
+    view_corange(c, A, K, F);            // A^T Q_c
+    orth(c, F, Rf);                      // [Q_r, R_r]
+    core_svd(c, Rf, Lk, W, Vj, Sv);      // R_r = V^ L U^T
+    write_outputs(c, K, Vj, F, W, Lk, Sv, k, o);
+  } else {
+    view_range(c, A, K, F);              // A Q_r
+    orth(c, F, Rf);                      // [Q_c, R_c]
+    core_svd(c, Rf, Lk, W, Vj, Sv);      // R_c = U^ L V^T
+    write_outputs(c, F, W, K, Vj, Lk, Sv, k, o);
+  }
+}
+
+// ------------------------------------------------------- Section 7.3
+void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o) {
+  LR_REQUIRE(ell <= kMaxBlock, LR_ERR_UNSUPPORTED, "row-streamed block Krylov needs ell <= 128");
+  ArenaScope sc(c.ar);
+  const int Lk = (v - 1) * ell;
+  Mat K{c.ar.take<float>(size_t(A.n) * Lk), A.n, Lk, A.n};
+  Mat Y{c.ar.take<float>(size_t(A.m) * ell), A.m, ell, A.m};
+  Mat Z{c.ar.take<float>(size_t(A.n) * ell), A.n, ell, A.n};
+  double* Rc = c.ar.take<double>(size_t(ell) * ell);
+  float* Ri = c.ar.take<float>(size_t(ell) * ell);
+  Mat F{c.ar.take<float>(size_t(A.m) * Lk), A.m, Lk, A.m};
+  double* Rf = c.ar.take<double>(size_t(Lk) * Lk);
+  float* W = c.ar.take<float>(size_t(Lk) * Lk);
+  float* Vj = c.ar.take<float>(size_t(Lk) * Lk);
+  float* Sv = c.ar.take<float>(size_t(Lk));
+  Mat x = Om;
+  for (int i = 1; i <= v - 1; ++i) {
+    view_chained(c, A, x, Y, Z);         // Y = A X, Z = A^T Y from one read
+    orth(c, Y, Rc);                      // Y = Q_c R_c
+    Mat blk{K.col(int64_t(i - 1) * ell), A.n, ell, A.n};
+    if (!c.measure) {
+      tri_inv(Rc, ell, ell, Ri, ell, c.status, c.s);
+      gemm(c, A.n, ell, ell, false, Z.p, Z.ld, false, Ri, ell, blk.p, blk.ld);  // A^T Q_c = Z R_c^{-1}
+    }
+    if (i < v - 1) orth(c, blk, nullptr, true);
+    x = blk;
+  }
+  orth(c, K, nullptr, true);             // Q_r = qr(K_r)
+  view_range(c, A, K, F);                // last view: A Q_r
+  orth(c, F, Rf);
+  core_svd(c, Rf, Lk, W, Vj, Sv);        // R_c = U^ L V^T
+  write_outputs(c, F, W, K, Vj, Lk, Sv, k, o);
+}
+
+// ------------------------------------------------------- Section 6.7
+void run_rowwise_qb(Ctx& c, const AMat& A, int k, int ell, const Mat& Om, Outs& o) {
+  LR_REQUIRE(ell <= kMaxBlock, LR_ERR_UNSUPPORTED, "row-streamed single pass needs ell <= 128");
+  ArenaScope sc(c.ar);
+  Mat Y{c.ar.take<float>(size_t(A.m) * ell), A.m, ell, A.m};
+  Mat Z{c.ar.take<float>(size_t(A.n) * ell), A.n, ell, A.n};
+  Mat Bt{c.ar.take<float>(size_t(A.n) * ell), A.n, ell, A.n};
+  double* Rc = c.ar.take<double>(size_t(ell) * ell);
+  double* Rb = c.ar.take<double>(size_t(ell) * ell);
+  float* Ri = c.ar.take<float>(size_t(ell) * ell);
+  float* W = c.ar.take<float>(size_t(ell) * ell);
+  float* Vj = c.ar.take<float>(size_t(ell) * ell);
+  float* Sv = c.ar.take<float>(size_t(ell));
+  view_chained(c, A, Om, Y, Z);          // Y_c = A Omega, Y^_r = A^T Y_c
+  orth(c, Y, Rc);                        // [Q_c, R_c] = qr(Y_c)
+  if (!c.measure) {
+    tri_inv(Rc, ell, ell, Ri, ell, c.status, c.s);
+    gemm(c, A.n, ell, ell, false, Z.p, Z.ld, false, Ri, ell, Bt.p, Bt.ld);  // B^T = Y^_r R_c^{-1}
+  }
+  orth(c, Bt, Rb);                       // B^T = Q_b R_b
+  core_svd(c, Rb, ell, W, Vj, Sv);       // R_b = V^ L U^T
+  write_outputs(c, Y, Vj, Bt, W, ell, Sv, k, o);
+}
+
+// ------------------------------------------------------------ Alg. 7
+void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const Mat& Psi, Outs& o) {
+  ArenaScope sc(c.ar);
+  const int ell1 = int(Om.cols), ell2 = int(Psi.cols);
+  const int l1 = ell1 - k;
+  const int lc = (l_c < 0 || l_c > l1) ? l1 : l_c;
+  const int Lc = k + lc;
+  LR_REQUIRE(Lc <= kMaxBlock, LR_ERR_UNSUPPORTED, "single pass needs k + l_c <= 128");
+  Mat Y{c.ar.take<float>(size_t(A.m) * ell1), A.m, ell1, A.m};
+  Mat Z{c.ar.take<float>(size_t(A.n) * ell2), A.n, ell2, A.n};
+  double* Rc = c.ar.take<double>(size_t(ell1) * ell1);
+  Mat Q2{lc < l1 ? c.ar.take<float>(size_t(A.m) * Lc) : nullptr, A.m, Lc, A.m};
+  float* Wc = c.ar.take<float>(size_t(ell1) * ell1);
+  float* Vc = c.ar.take<float>(size_t(ell1) * ell1);
+  float* Sc = c.ar.take<float>(size_t(ell1));
+  double* P64 = c.ar.take<double>(size_t(ell2) * Lc);
+  Mat P{c.ar.take<float>(size_t(ell2) * Lc), ell2, Lc, ell2};
+  double* Rh = c.ar.take<double>(size_t(Lc) * Lc);
+  float* Rhi = c.ar.take<float>(size_t(Lc) * Lc);
+  Mat Wz{c.ar.take<float>(size_t(A.n) * Lc), A.n, Lc, A.n};
+  Mat Xt{c.ar.take<float>(size_t(A.n) * Lc), A.n, Lc, A.n};
+  double* Rx = c.ar.take<double>(size_t(Lc) * Lc);
+  float* W = c.ar.take<float>(size_t(Lc) * Lc);
+  float* Vj = c.ar.take<float>(size_t(Lc) * Lc);
+  float* Sv = c.ar.take<float>(size_t(Lc));
+
+  view_dual(c, A, Om, Y, Psi, Z);        // a) Y_c = A Omega_r, b) Y_r = A^T Omega_c
+  orth(c, Y, Rc);                        // [Q_c, R_c] = qr(Y_c)
+  Mat Qc = Y;
+  if (lc < l1) {
+    core_svd(c, Rc, ell1, Wc, Vc, Sc);   // leading k + l_c left vectors of R_c
+    gemm(c, A.m, Lc, ell1, false, Y.p, Y.ld, false, Wc, ell1, Q2.p, Q2.ld);
+    Qc = Q2;
+  }
+  gram64(c, ell2, Lc, A.m, Psi.p, Psi.ld, Qc.p, Qc.ld, P64, ell2);   // Omega_c^T Q_c
+  if (!c.measure) f64_to_f32(P64, ell2, P.p, P.ld, ell2, Lc, c.s);
+  orth(c, P, Rh);                        // [Q^, R^] = qr(Omega_c^T Q_c)
+  gemm(c, A.n, Lc, ell2, false, Z.p, Z.ld, false, P.p, P.ld, Wz.p, Wz.ld);  // Y_r Q^
+  if (!c.measure) tri_inv(Rh, Lc, Lc, Rhi, Lc, c.status, c.s);
+  gemm(c, A.n, Lc, Lc, false, Wz.p, Wz.ld, true, Rhi, Lc, Xt.p, Xt.ld);    // X^T = Y_r Q^ R^{-T}
+  orth(c, Xt, Rx);                       // X^T = Q_x R_x
+  core_svd(c, Rx, Lc, W, Vj, Sv);        // R_x = W S Vj^T, X = Vj S (Q_x W)^T
+  write_outputs(c, Qc, Vj, Xt, W, Lc, Sv, k, o);
+}
+
+// ------------------------------------------------------- validation
+AMat check_A(const lr_mat* A) {
+  LR_REQUIRE(A && A->data, LR_ERR_INVALID_ARG, "A is NULL");
+  LR_REQUIRE(A->dtype == LR_F32 || A->dtype == LR_BF16, LR_ERR_DTYPE, "A must be F32 or BF16");
+  LR_REQUIRE(A->col_major == 0, LR_ERR_DTYPE, "A must be row-major");
+  LR_REQUIRE(A->rows >= 1 && A->cols >= 1 && A->ld >= A->cols, LR_ERR_SHAPE, "bad A shape");
+  AMat a;
+  a.p = A->data;
+  a.m = A->rows;
+  a.n = A->cols;
+  a.ld = A->ld;
+  a.bf16 = A->dtype == LR_BF16;
+  LR_REQUIRE((reinterpret_cast<uintptr_t>(A->data) & 15) == 0, LR_ERR_ALIGNMENT, "A not 16-byte aligned");
+  LR_REQUIRE((A->ld * int64_t(a.elem())) % 16 == 0, LR_ERR_ALIGNMENT, "A row stride not a multiple of 16 bytes");
+  return a;
+}
+
+Mat check_thin(const lr_mat* X, int64_t rows, int64_t cols, const char* name) {
+  LR_REQUIRE(X && X->data, LR_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  LR_REQUIRE(X->dtype == LR_F32, LR_ERR_DTYPE, std::string(name) + " must be F32");
+  LR_REQUIRE(X->col_major == 1, LR_ERR_DTYPE, std::string(name) + " must be column-major");
+  LR_REQUIRE(X->rows == rows && (cols < 0 || X->cols == cols) && X->ld >= X->rows, LR_ERR_SHAPE,
+             std::string(name) + " has the wrong shape");
+  return Mat{static_cast<float*>(X->data), X->rows, X->cols, X->ld};
+}
+
+Outs check_outs(const AMat& A, int k, lr_mat* U, lr_mat* S, lr_mat* V) {
+  Outs o;
+  o.U = check_thin(U, A.m, k, "U");
+  o.V = check_thin(V, A.n, k, "V");
+  LR_REQUIRE(S && S->data, LR_ERR_INVALID_ARG, "S is NULL");
+  LR_REQUIRE(S->dtype == LR_F32, LR_ERR_DTYPE, "S must be F32");
+  LR_REQUIRE(S->rows * S->cols >= k, LR_ERR_SHAPE, "S too short");
+  o.S = S->data;
+  return o;
+}
+
+lr_status finish(lr_handle h, const Error& e) {
+  if (h) h->last_error = e.msg;
+  return e.st;
+}
+
+Ctx make_ctx(lr_handle h, const lr_opts* opts, void* stream) {
+  Ctx c;
+  c.h = h;
+  c.s = static_cast<cudaStream_t>(stream);
+  c.ar.base = static_cast<char*>(h->ws);
+  c.ar.cap = h->ws_bytes;
+  c.sms = dev_info(h->device).sms;
+  c.status = h->status_dev;
+  if (opts) c.opt = *opts;
+  else c.opt.l_c = -1;
+  LR_CHECK_CUDA(cudaSetDevice(h->device));
+  return c;
+}
+
+template <class F>
+lr_status guarded(lr_handle h, F&& f) {
+  if (!h) return LR_ERR_INVALID_ARG;
+  try {
+    h->last_error.clear();
+    f();
+    return LR_OK;
+  } catch (const Error& e) {
+    return finish(h, e);
+  } catch (const std::exception& e) {
+    return finish(h, Error{LR_ERR_INVALID_ARG, e.what()});
+  }
+}
+
+void check_kpv(const AMat& A, int k, int p, int v, int vmin) {
+  LR_REQUIRE(k >= 1 && p >= 0, LR_ERR_INVALID_ARG, "need k >= 1 and p >= 0");
+  LR_REQUIRE(k + p <= std::min(A.m, A.n), LR_ERR_INVALID_ARG, "need k + p <= min(m, n)");
+  LR_REQUIRE(v >= vmin, LR_ERR_INVALID_ARG, "too few views");
+}
+
+}  // namespace
+}  // namespace lr
+
+using namespace lr;
+
+extern "C" {
+
+lr_status lr_create(lr_handle* handle, int device) {
+  if (!handle) return LR_ERR_INVALID_ARG;
+  *handle = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return LR_ERR_INVALID_ARG;
+  auto* h = new lr_handle_s();
+  h->device = device;
+  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&h->status_dev, sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->status_dev, 0, sizeof(int)) != cudaSuccess) {
+    delete h;
+    return LR_ERR_CUDA;
+  }
+  *handle = h;
+  return LR_OK;
+}
+
+lr_status lr_destroy(lr_handle h) {
+  if (!h) return LR_ERR_INVALID_ARG;
+  cudaSetDevice(h->device);
+  cudaFree(h->status_dev);
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  delete h;
+  return LR_OK;
+}
+
+const char* lr_status_string(lr_status st) {
+  switch (st) {
+    case LR_OK: return "ok";
+    case LR_ERR_INVALID_ARG: return "invalid argument";
+    case LR_ERR_SHAPE: return "inconsistent shape";
+    case LR_ERR_DTYPE: return "unsupported dtype or layout";
+    case LR_ERR_ALIGNMENT: return "misaligned pointer or stride";
+    case LR_ERR_BREAKDOWN: return "Cholesky breakdown (rank-deficient sketch)";
+    case LR_ERR_NONFINITE: return "non-finite value";
+    case LR_ERR_TIMEOUT: return "device-side wait timed out";
+    case LR_ERR_CUDA: return "CUDA error";
+    case LR_ERR_NOMEM: return "workspace missing or too small";
+    case LR_ERR_UNSUPPORTED: return "unsupported by this build";
+  }
+  return "unknown status";
+}
+
+const char* lr_last_error(lr_handle h) { return h ? h->last_error.c_str() : ""; }
+
+lr_status lr_set_workspace(lr_handle h, void* ptr, size_t bytes) {
+  if (!h) return LR_ERR_INVALID_ARG;
+  if (bytes && (!ptr || (reinterpret_cast<uintptr_t>(ptr) & 255))) return LR_ERR_ALIGNMENT;
+  h->ws = ptr;
+  h->ws_bytes = bytes;
+  return LR_OK;
+}
+
+lr_status lr_get_status(lr_handle h, void* stream, int* device_status) {
+  return guarded(h, [&] {
+    LR_REQUIRE(device_status, LR_ERR_INVALID_ARG, "device_status is NULL");
+    LR_CHECK_CUDA(cudaSetDevice(h->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    LR_CHECK_CUDA(cudaMemcpyAsync(&v, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LR_CHECK_CUDA(cudaStreamSynchronize(s));
+    LR_CHECK_CUDA(cudaMemsetAsync(h->status_dev, 0, sizeof(int), s));
+    LR_CHECK_CUDA(cudaStreamSynchronize(s));
+    *device_status = v;
+  });
+}
+
+lr_status lr_workspace_size(lr_handle h, int64_t m, int64_t n, int ell1, int ell2, int v, size_t* bytes) {
+  return guarded(h, [&] {
+    LR_REQUIRE(bytes && m > 0 && n > 0 && ell1 > 0 && v >= 1, LR_ERR_INVALID_ARG, "bad workspace query");
+    size_t best = 0;
+    const int vv = std::max(v, 2);
+    for (int bf = 0; bf < 2; ++bf) {
+      AMat A;
+      A.m = m; A.n = n; A.ld = n; A.bf16 = bf == 1;
+      // Each schedule's allocation sequence is replayed without launches;
+      // schedules these sizes cannot run (e.g. widths over a limit) are
+      // skipped rather than failing the query.
+      auto measure = [&](auto&& body) {
+        Ctx c;
+        c.h = h;
+        c.measure = true;
+        c.ar.measure = true;
+        c.sms = 1;
+        c.opt.shifted_fallback = 1;
+        try {
+          body(c);
+        } catch (const Error&) {
+        }
+        best = std::max(best, c.ar.peak);
+      };
+      Mat Om{nullptr, n, ell1, n};
+      Outs o;
+      const int k = 1;
+      measure([&](Ctx& c) { run_subspace(c, A, k, ell1, vv, Om, o); });
+      measure([&](Ctx& c) { run_krylov(c, A, k, ell1, vv, Om, o); });
+      if (ell1 <= kMaxBlock) {
+        measure([&](Ctx& c) { run_krylov_rowwise(c, A, k, ell1, vv, Om, o); });
+        measure([&](Ctx& c) { run_rowwise_qb(c, A, k, ell1, Om, o); });
+      }
+      if (ell2 >= ell1) {
+        Mat Ps{nullptr, m, ell2, m};
+        measure([&](Ctx& c) { run_single_pass(c, A, std::max(1, ell1 - 1), -1, Om, Ps, o); });
+      }
+      measure([&](Ctx& c) {
+        Mat Y{nullptr, m, std::max(ell1, ell2), m};
+        orth(c, Y, nullptr);
+        Mat Zm{nullptr, n, ell2 > 0 ? ell2 : ell1, n};
+        view_dual(c, A, Om, Y, Y, Zm);
+        view_chained(c, A, Om, Y, Zm);
+      });
+    }
+    *bytes = best + 4096;
+  });
+}
+
+lr_status lr_sketch(lr_handle h, const lr_mat* A, const lr_mat* X, const lr_mat* W, lr_mat* Y, lr_mat* Z,
+                    const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    Ctx c = make_ctx(h, opts, stream);
+    LR_REQUIRE(X || W, LR_ERR_INVALID_ARG, "need X or W");
+    Mat x, y, w, z;
+    if (X) {
+      x = check_thin(X, a.n, -1, "X");
+      y = check_thin(Y, a.m, x.cols, "Y");
+    }
+    if (W) {
+      w = check_thin(W, a.m, -1, "W");
+      z = check_thin(Z, a.n, w.cols, "Z");
+    }
+    if (X && W) view_dual(c, a, x, y, w, z);
+    else if (X) view_range(c, a, x, y);
+    else view_corange(c, a, w, z);
+  });
+}
+
+lr_status lr_sketch_chained(lr_handle h, const lr_mat* A, const lr_mat* X, lr_mat* Y, lr_mat* Z, const lr_opts* opts,
+                            void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    Ctx c = make_ctx(h, opts, stream);
+    Mat x = check_thin(X, a.n, -1, "X");
+    Mat y = check_thin(Y, a.m, x.cols, "Y");
+    Mat z = check_thin(Z, a.n, x.cols, "Z");
+    view_chained(c, a, x, y, z);
+  });
+}
+
+lr_status lr_orth(lr_handle h, lr_mat* Y, lr_mat* R, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    LR_REQUIRE(Y, LR_ERR_INVALID_ARG, "Y is NULL");
+    Mat y = check_thin(Y, Y->rows, -1, "Y");
+    LR_REQUIRE(y.rows >= y.cols && y.cols >= 1, LR_ERR_SHAPE, "orth needs rows >= cols >= 1");
+    double* r = nullptr;
+    if (R) {
+      LR_REQUIRE(R->data && R->dtype == LR_F64 && R->rows == y.cols && R->cols == y.cols && R->ld == y.cols,
+                 LR_ERR_SHAPE, "R must be a dense ell x ell F64 matrix");
+      r = static_cast<double*>(R->data);
+    }
+    Ctx c = make_ctx(h, opts, stream);
+    orth(c, y, r);
+  });
+}
+
+lr_status lr_subspace_iter(lr_handle h, const lr_mat* A, int k, int p, int v, const lr_mat* Omega, lr_mat* U,
+                           lr_mat* S, lr_mat* V, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    check_kpv(a, k, p, v, 2);
+    Mat om = check_thin(Omega, a.n, k + p, "Omega");
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    run_subspace(c, a, k, k + p, v, om, o);
+  });
+}
+
+lr_status lr_block_krylov(lr_handle h, const lr_mat* A, int k, int p, int v, const lr_mat* Omega, lr_mat* U,
+                          lr_mat* S, lr_mat* V, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    check_kpv(a, k, p, v, 2);
+    Mat om = check_thin(Omega, a.n, k + p, "Omega");
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    const bool enhanced = opts && opts->enhanced;
+    const int ell = k + p;
+    if (enhanced) {
+      LR_REQUIRE(int64_t(v - 1) * ell <= std::min(a.m, a.n), LR_ERR_INVALID_ARG, "Krylov basis wider than A");
+      run_krylov_rowwise(c, a, k, ell, v, om, o);
+    } else {
+      const int nb = (v % 2 == 0) ? v / 2 : (v - 1) / 2;
+      LR_REQUIRE(int64_t(nb) * ell <= std::min(a.m, a.n), LR_ERR_INVALID_ARG, "Krylov basis wider than A");
+      run_krylov(c, a, k, ell, v, om, o);
+    }
+  });
+}
+
+lr_status lr_rowwise_single_pass(lr_handle h, const lr_mat* A, int k, const lr_mat* Omega, lr_mat* U, lr_mat* S,
+                                 lr_mat* V, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    LR_REQUIRE(Omega, LR_ERR_INVALID_ARG, "Omega is NULL");
+    const int ell = int(Omega->cols);
+    check_kpv(a, k, ell - k, 1, 1);
+    Mat om = check_thin(Omega, a.n, ell, "Omega");
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    run_rowwise_qb(c, a, k, ell, om, o);
+  });
+}
+
+lr_status lr_single_pass(lr_handle h, const lr_mat* A, int k, const lr_mat* Omega, const lr_mat* Psi, lr_mat* U,
+                         lr_mat* S, lr_mat* V, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    LR_REQUIRE(Omega && Psi, LR_ERR_INVALID_ARG, "Omega and Psi are required");
+    Mat om = check_thin(Omega, a.n, -1, "Omega");
+    Mat ps = check_thin(Psi, a.m, -1, "Psi");
+    LR_REQUIRE(k >= 1 && om.cols > k, LR_ERR_INVALID_ARG, "need ell1 > k");
+    LR_REQUIRE(ps.cols >= om.cols, LR_ERR_INVALID_ARG, "need ell2 >= ell1 (l_2 >= l_1)");
+    LR_REQUIRE(ps.cols <= std::min(a.m, a.n), LR_ERR_INVALID_ARG, "ell2 larger than min(m, n)");
+    const int lc = opts ? opts->l_c : -1;
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    run_single_pass(c, a, k, lc, om, ps, o);
+  });
+}
+
+lr_status lr_single_pass_host(lr_handle h, const lr_mat*, int64_t, int, const lr_mat*, const lr_mat*, lr_mat*,
+                              lr_mat*, lr_mat*, const lr_opts*, void*) {
+  return guarded(h, [&] { throw Error{LR_ERR_UNSUPPORTED, "host-streamed single pass is not built yet"}; });
+}
+
+lr_status lr_subspace_iter_backward(lr_handle h, const lr_mat*, int, int, int, const lr_mat*, const lr_mat*, lr_mat*,
+                                    const lr_opts*, void*) {
+  return guarded(h, [&] { throw Error{LR_ERR_UNSUPPORTED, "backward is not built yet"}; });
+}
+
+lr_status lr_set_trace(lr_handle h, int on) {
+  return guarded(h, [&] {
+    LR_CHECK_CUDA(cudaSetDevice(h->device));
+    if (on && h->pool.empty()) {
+      h->pool.resize(8192);
+      for (auto& e : h->pool) LR_CHECK_CUDA(cudaEventCreate(&e));
+      h->recs.reserve(4096);
+    }
+    h->trace = on != 0;
+  });
+}
+
+lr_status lr_trace_read(lr_handle h, int kind, double* total_ms, int64_t* launches, int reset) {
+  return guarded(h, [&] {
+    LR_REQUIRE(kind >= 0 && kind < LR_TRACE_COUNT && total_ms && launches, LR_ERR_INVALID_ARG, "bad trace query");
+    LR_CHECK_CUDA(cudaSetDevice(h->device));
+    LR_CHECK_CUDA(cudaDeviceSynchronize());
+    for (const auto& r : h->recs) {
+      float ms = 0.f;
+      LR_CHECK_CUDA(cudaEventElapsedTime(&ms, r.begin, r.end));
+      h->acc_ms[r.kind] += ms;
+      h->acc_n[r.kind] += 1;
+    }
+    h->recs.clear();
+    h->pool_used = 0;
+    *total_ms = h->acc_ms[kind];
+    *launches = h->acc_n[kind];
+    if (reset) {
+      for (int i = 0; i < LR_TRACE_COUNT; ++i) {
+        h->acc_ms[i] = 0.0;
+        h->acc_n[i] = 0;
+      }
+    }
+  });
+}
+
+lr_status lr_kernel_launches(lr_handle h, uint64_t* count) {
+  if (!h || !count) return LR_ERR_INVALID_ARG;
+  *count = g_kernel_launches.load();
+  return LR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Internal launchers of liblowrank (not part of the C ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lr {
+
+// ------------------------------------------------------------ SIMT GEMM
+enum GemmMode { GEMM_STORE = 0, GEMM_ATOMIC_F32 = 1, GEMM_ATOMIC_F64 = 2 };
+struct GemmArgs {
+  int64_t M = 0, N = 0, K = 0;
+  bool ta = false, tb = false;
+  float alpha = 1.f, beta = 0.f;
+  const float* A = nullptr;
+  int64_t lda = 0;
+  const float* B = nullptr;
+  int64_t ldb = 0;
+  float* C = nullptr;
+  double* C64 = nullptr;
+  int64_t ldc = 0;
+  int mode = GEMM_STORE;
+  int split_k = 1;
+};
+void sgemm(const GemmArgs& g, cudaStream_t s);
+int split_for(int64_t M, int64_t N, int64_t K, int sms);
+
+// ------------------------------------------------------- tensor-core views
+struct ViewBf16Args {
+  int device = 0;
+  int mode = 0;  // 0: out[row0 + i] += A[row0 + i, :] B ; 1: out += A[band]^T B[band]
+  const __nv_bfloat16* A = nullptr;
+  int64_t lda = 0, row0 = 0, rows = 0, n = 0;
+  const __nv_bfloat16* B = nullptr;  // col-major thin operand: n x ell (mode 0) or the band's rows x ell (mode 1)
+  int64_t ldb = 0;
+  int ell = 0;
+  float* out = nullptr;  // col-major FP32, pre-zeroed (partials are added)
+  int64_t ldo = 0;
+  int* status = nullptr;
+};
+void view_bf16(const ViewBf16Args& a, cudaStream_t s);
+int view_bf16_ncol(int ell);
+
+// ---------------------------------------------------------- elementwise
+void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s);
+void zero_bytes(void* p, size_t bytes, cudaStream_t s);
+// dst (bf16, col-major rows x cols, ldd) = round(src); with lo != nullptr
+// also lo = round(src - hi) (the hi/lo split of a thin operand).
+void f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, __nv_bfloat16* lo, int64_t ldd, int64_t rows,
+                 int64_t cols, cudaStream_t s);
+void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s);
+// dst row-major = src^T for an F32 col-major src (rows x cols) -> (cols x rows)
+void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n, int k, cudaStream_t s);
+
+// ---------------------------------------------------- small dense kernels
+// Cholesky of an FP64-accumulated Gram (ell <= 128) in one CTA:
+//   G (ell x ell, FP64 col-major, ld ell) = R^T R; writes Rinv (FP32,
+//   ell x ell, ldr); Racc (FP64, ldacc) <- R (init_acc) or R * Racc.
+//   Racc may be nullptr.  Breakdown / non-finite -> status.
+void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int shifted,
+              int* status, cudaStream_t s);
+// X = R^{-1} (FP32) for an upper-triangular FP64 R (n <= 128).
+void tri_inv(const double* R, int ldr, int n, float* X, int ldx, int* status, cudaStream_t s);
+// R (ell x ell FP64) block (rows r0.., cols c0..) += C (FP64 in, col-major)
+void add_block_f64(double* R, int ldr, int r0, int c0, const double* C, int ldc, int rows, int cols, cudaStream_t s);
+void f64_to_f32(const double* src, int lds, float* dst, int ldd, int rows, int cols, cudaStream_t s);
+// One-sided Jacobi SVD of M (rows x cols, FP32 col-major, rows >= cols):
+//   M = U diag(S) V^T; U overwrites Wk (rows x cols), V (cols x cols), S desc.
+void jacobi_svd(const float* M, int ldm, int rows, int cols, float* Wk, int ldw, float* V, int ldv, float* S,
+                double* S64, int* status, cudaStream_t s);
+// Copy a square FP64 upper-triangular R into FP32 (transposed if trans).
+void r_to_f32(const double* R, int ldr, int n, float* out, int ldo, bool trans, cudaStream_t s);
+// Small dense QR helper for the single-pass core: see single_pass driver.
+void scale_cols_f32(float* A, int64_t lda, int64_t rows, int cols, const float* scale, cudaStream_t s);
+
+}  // namespace lr

@@ -1,0 +1,560 @@
+// Small dense kernels: the ell x ell factorisations between views and
+// elementwise helpers.
+//
+// GB300's FP64 pipe runs at about 1/60 of its FP32 rate (1.25 TFLOP/s per
+// GPU), so O(ell^3) work in FP64 on one SM would cost milliseconds.  The
+// Grams reach these kernels FP64-accumulated (their dominant error, the
+// m-term summation, is gone); the Cholesky, the triangular inverse and the
+// core SVD then run in FP32 inside one CTA with the matrix in shared memory.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lr {
+
+namespace {
+
+__global__ void zero_kernel(float* p, int64_t rows, int64_t cols, int64_t ld) {
+  int64_t total = rows * cols;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t r = i % rows, c = i / rows;
+    p[r + c * ld] = 0.f;
+  }
+}
+
+__global__ void f32_to_bf16_kernel(const float* __restrict__ src, int64_t lds, __nv_bfloat16* __restrict__ dst,
+                                   __nv_bfloat16* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols) {
+  int64_t total = rows * cols;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t r = i % rows, c = i / rows;
+    float x = src[r + c * lds];
+    __nv_bfloat16 h = __float2bfloat16_rn(x);
+    dst[r + c * ldd] = h;
+    if (lo) lo[r + c * ldd] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+__global__ void copy_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ dst, int64_t ldd,
+                            int64_t rows, int64_t cols) {
+  int64_t total = rows * cols;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t r = i % rows, c = i / rows;
+    dst[r + c * ldd] = src[r + c * lds];
+  }
+}
+
+// One block per column i: find the entry of U(:, i) with the largest
+// magnitude (lowest index on ties) and flip (u_i, v_i) if it is negative.
+__global__ void fix_signs_kernel(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n) {
+  const int col = blockIdx.x;
+  float* u = U + col * ldu;
+  float best = -1.f;
+  int64_t bidx = 0;
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+    float a = fabsf(u[r]);
+    if (a > best) { best = a; bidx = r; }
+  }
+  __shared__ float sb[32];
+  __shared__ int64_t si[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    float ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int64_t oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) { sb[w] = best; si[w] = bidx; }
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x / 32;
+    best = l < nw ? sb[l] : -1.f;
+    bidx = l < nw ? si[l] : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+      float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int64_t oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
+    }
+    if (l == 0) si[0] = bidx;
+  }
+  __syncthreads();
+  const bool flip = u[si[0]] < 0.f;
+  __syncthreads();
+  if (!flip) return;
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) u[r] = -u[r];
+  float* v = V + col * ldv;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) v[r] = -v[r];
+}
+
+// Upper-triangular inverse of R (n x n, column-major FP32 in smem, lda n):
+// X = R^{-1} row by row from the bottom: X(i,i) = 1/R(i,i),
+// X(i,j) = -(sum_{k=i+1..j} R(i,k) X(k,j)) / R(i,i) for j > i.
+// Rows are processed in decreasing i; the n-i entries of row i are computed
+// in parallel, each dot product split over 8 threads.
+__device__ void upper_inverse_smem(const float* R, float* X, int n) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * n; idx += nt) X[idx] = 0.f;
+  __syncthreads();
+  for (int i = n - 1; i >= 0; --i) {
+    const float rii = R[i + i * n];
+    // (n - i) outputs, 8 threads each; the loop trip count is the same for
+    // every thread so whole warps execute the shuffles.
+    const int work = (n - i) * 8;
+    for (int t0 = 0; t0 < work; t0 += nt) {
+      const int t = t0 + tid;
+      const bool act = t < work;
+      const int j = i + t / 8, part = t % 8;
+      float acc = 0.f;
+      if (act)
+        for (int k = i + 1 + part; k <= j; k += 8) acc = fmaf(R[i + k * n], X[k + j * n], acc);
+      acc += __shfl_down_sync(0xffffffffu, acc, 4, 8);
+      acc += __shfl_down_sync(0xffffffffu, acc, 2, 8);
+      acc += __shfl_down_sync(0xffffffffu, acc, 1, 8);
+      if (act && part == 0) X[i + j * n] = (j == i) ? 1.f / rii : -acc / rii;
+    }
+    __syncthreads();
+  }
+}
+
+// Cholesky G = R^T R (G FP64 in global, computed in FP32 in shared memory),
+// then Rinv = R^{-1} and Racc <- R Racc (or Racc = R when init).
+// Shared memory: 3 n x n FP32 matrices (n <= 128 -> 192 KB).
+__global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ G, int n, float* Rinv, int ldr,
+                                                        double* Racc, int ldacc, int init_acc, int shifted,
+                                                        int* status) {
+  extern __shared__ float sm[];
+  float* L = sm;            // lower Cholesky factor L = R^T, col-major n x n
+  float* X = sm + n * n;    // R^{-1}
+  float* T = X + n * n;     // scratch (R as upper, col-major)
+  __shared__ int bad;
+  __shared__ float shift;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    bad = 0;
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += G[i + i * n];
+    // Shifted CholeskyQR (Fukaya et al. 2020): G + s I with s a small
+    // multiple of |G| (trace as the estimate), above the FP32 Gram and
+    // Cholesky rounding level, so the factorisation cannot break down; the
+    // following unshifted passes restore orthogonality.
+    shift = shifted ? float(1e-5 * tr) : 0.f;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    const double g = G[idx];
+    if (!isfinite(g)) bad = LR_ERR_NONFINITE;
+    L[idx] = (r >= c) ? float(g) + (r == c ? shift : 0.f) : 0.f;
+  }
+  __syncthreads();
+  for (int j = 0; j < n && !bad; ++j) {
+    if (tid == 0) {
+      const float d = L[j + j * n];
+      if (!(d > 0.f) || !isfinite(d)) bad = LR_ERR_BREAKDOWN;
+      else L[j + j * n] = sqrtf(d);
+    }
+    __syncthreads();
+    if (bad) break;
+    const float ljj = L[j + j * n];
+    for (int i = j + 1 + tid; i < n; i += nt) L[i + j * n] /= ljj;
+    __syncthreads();
+    // trailing update of the lower triangle: L(i,c) -= L(i,j) L(c,j), j < c <= i
+    const int m = n - j - 1;
+    for (int idx = tid; idx < m * m; idx += nt) {
+      const int c = j + 1 + idx / m, i = j + 1 + idx % m;
+      if (i >= c) L[i + c * n] -= L[i + j * n] * L[c + j * n];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (tid == 0) set_status(status, bad);
+    // leave a harmless identity so later kernels stay finite
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx % n, c = idx / n;
+      Rinv[r + c * ldr] = (r == c) ? 1.f : 0.f;
+    }
+    return;
+  }
+  // T = R = L^T (upper)
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    T[idx] = (r <= c) ? L[c + r * n] : 0.f;
+  }
+  __syncthreads();
+  upper_inverse_smem(T, X, n);
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    Rinv[r + c * ldr] = X[idx];
+  }
+  if (Racc) {
+    if (init_acc) {
+      for (int idx = tid; idx < n * n; idx += nt) {
+        const int r = idx % n, c = idx / n;
+        Racc[r + c * ldacc] = double(T[idx]);
+      }
+    } else {
+      // L <- Racc (FP32 copy), then Racc = T * L (both upper)
+      __syncthreads();
+      for (int idx = tid; idx < n * n; idx += nt) {
+        const int r = idx % n, c = idx / n;
+        L[idx] = (r <= c) ? float(Racc[r + c * ldacc]) : 0.f;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < n * n; idx += nt) {
+        const int r = idx % n, c = idx / n;
+        float acc = 0.f;
+        if (r <= c)
+          for (int k = r; k <= c; ++k) acc = fmaf(T[r + k * n], L[k + c * n], acc);
+        Racc[r + c * ldacc] = double(acc);
+      }
+    }
+  }
+}
+
+// Inverse of an upper-triangular FP64 R (n x n, n <= 128) into FP32.
+__global__ void __launch_bounds__(1024) tri_inv_kernel(const double* __restrict__ R, int ldr, int n, float* X,
+                                                       int ldx, int* status) {
+  extern __shared__ float sm[];
+  float* T = sm;
+  float* Y = sm + n * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx % n, c = idx / n;
+    T[idx] = (r <= c) ? float(R[r + c * ldr]) : 0.f;
+    if (r == c && !(T[idx] != 0.f)) set_status(status, LR_ERR_BREAKDOWN);
+  }
+  __syncthreads();
+  upper_inverse_smem(T, Y, n);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx % n, c = idx / n;
+    X[r + c * ldx] = Y[idx];
+  }
+}
+
+__global__ void add_block_kernel(double* R, int ldr, int r0, int c0, const double* C, int ldc, int rows, int cols) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * cols; idx += gridDim.x * blockDim.x) {
+    const int r = idx % rows, c = idx / rows;
+    R[(r0 + r) + int64_t(c0 + c) * ldr] += C[r + int64_t(c) * ldc];
+  }
+}
+
+__global__ void f64_to_f32_kernel(const double* src, int lds, float* dst, int ldd, int rows, int cols) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * cols; idx += gridDim.x * blockDim.x) {
+    const int r = idx % rows, c = idx / rows;
+    dst[r + int64_t(c) * ldd] = float(src[r + int64_t(c) * lds]);
+  }
+}
+
+__global__ void r_to_f32_kernel(const double* R, int ldr, int n, float* out, int ldo, int trans) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int r = idx % n, c = idx / n;
+    const double v = (r <= c) ? R[r + int64_t(c) * ldr] : 0.0;
+    if (trans) out[c + int64_t(r) * ldo] = float(v);
+    else out[r + int64_t(c) * ldo] = float(v);
+  }
+}
+
+__global__ void scale_cols_kernel(float* A, int64_t lda, int64_t rows, int cols, const float* scale) {
+  int64_t total = rows * cols;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    int64_t r = i % rows, c = i / rows;
+    A[r + c * lda] *= scale[c];
+  }
+}
+
+// --------------------------------------------------------- Jacobi SVD
+// One-sided (Hestenes) Jacobi in one CTA.  W (rows x cols) starts as M and
+// V as the identity; each round of the circle-method ordering rotates
+// disjoint column pairs (one warp per pair) until a sweep makes no rotation:
+//   alpha = |w_p|^2, beta = |w_q|^2, gamma = w_p . w_q,
+//   rotate when |gamma| > tol sqrt(alpha beta),
+//   zeta = (beta - alpha) / (2 gamma), t = sign(zeta)/(|zeta| + sqrt(1+zeta^2)),
+//   c = 1/sqrt(1+t^2), s = c t, [w_p, w_q] <- [c w_p - s w_q, s w_p + c w_q].
+// Then s_i = |w_i|, u_i = w_i / s_i, sorted descending.  W and V live in
+// shared memory when they fit, else in the global buffers.
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ M, int ldm, int rows, int cols,
+                                                      float* Wg, int ldw, float* Vg, int ldv, float* S, double* S64,
+                                                      int* status) {
+  extern __shared__ float sm[];
+  float* W = SMEM ? sm : Wg;
+  const int ldW = SMEM ? rows : ldw;
+  float* V = SMEM ? sm + rows * cols : Vg;
+  const int ldV = SMEM ? cols : ldv;
+  __shared__ int rotated;
+  __shared__ float norms[1024];
+  __shared__ int order[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid / 32, lane = tid % 32, nwarps = nt / 32;
+  for (int idx = tid; idx < rows * cols; idx += nt) {
+    const int r = idx % rows, c = idx / rows;
+    W[r + c * ldW] = M[r + int64_t(c) * ldm];
+  }
+  for (int idx = tid; idx < cols * cols; idx += nt) {
+    const int r = idx % cols, c = idx / cols;
+    V[r + c * ldV] = (r == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const float tol = 1.2e-7f * sqrtf(float(rows));
+  const int np = cols + (cols & 1);  // even number of positions
+  const int npairs = np / 2;
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int pi = warp; pi < npairs; pi += nwarps) {
+        // circle method: s_0 = 0, s_k = 1 + (k - 1 + rnd) mod (np - 1)
+        int a = (pi == 0) ? 0 : 1 + (pi - 1 + rnd) % (np - 1);
+        int b = 1 + (np - 2 - pi + rnd) % (np - 1);
+        int p = min(a, b), q = max(a, b);
+        if (q >= cols) continue;
+        float* wp = W + p * ldW;
+        float* wq = W + q * ldW;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int r = lane; r < rows; r += 32) {
+          const float x = wp[r], y = wq[r];
+          al = fmaf(x, x, al);
+          be = fmaf(y, y, be);
+          ga = fmaf(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+          const float zeta = (be - al) / (2.f * ga);
+          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          // correctly rounded sqrt and division keep c^2 + s^2 = 1 to an
+          // unbiased half ulp, so V drifts from orthogonality only as a
+          // random walk over the rotations
+          const float c = 1.f / sqrtf(1.f + t * t);
+          const float s = c * t;
+          for (int r = lane; r < rows; r += 32) {
+            const float x = wp[r], y = wq[r];
+            wp[r] = c * x - s * y;
+            wq[r] = s * x + c * y;
+          }
+          float* vp = V + p * ldV;
+          float* vq = V + q * ldV;
+          for (int r = lane; r < cols; r += 32) {
+            const float x = vp[r], y = vq[r];
+            vp[r] = c * x - s * y;
+            vq[r] = s * x + c * y;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (sweep == 40 && tid == 0) set_status(status, LR_ERR_NONFINITE);
+  // Columns of V are unit vectors in exact arithmetic; remove the norm drift
+  // accumulated over the rotations.
+  for (int c = warp; c < cols; c += nwarps) {
+    float acc = 0.f;
+    for (int r = lane; r < cols; r += 32) acc = fmaf(V[r + c * ldV], V[r + c * ldV], acc);
+    acc = warp_sum(acc);
+    const float inv = 1.f / sqrtf(acc);
+    for (int r = lane; r < cols; r += 32) V[r + c * ldV] *= inv;
+  }
+  __syncthreads();
+  // norms and descending order (stable: ties keep the lower index first)
+  for (int c = warp; c < cols; c += nwarps) {
+    float acc = 0.f;
+    for (int r = lane; r < rows; r += 32) acc = fmaf(W[r + c * ldW], W[r + c * ldW], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) norms[c] = sqrtf(acc);
+  }
+  __syncthreads();
+  for (int c = tid; c < cols; c += nt) {
+    int rank = 0;
+    const float v = norms[c];
+    for (int d = 0; d < cols; ++d) {
+      const float o = norms[d];
+      rank += (o > v) || (o == v && d < c);
+    }
+    order[rank] = c;
+  }
+  __syncthreads();
+  // Outputs: S, U into Wg (normalised, permuted), V into Vg (permuted).
+  // In the smem case the global buffers are free to write directly.  In the
+  // global case W/V alias the outputs, so the permutation goes through a
+  // column at a time with a barrier.
+  if (SMEM) {
+    for (int idx = tid; idx < rows * cols; idx += nt) {
+      const int r = idx % rows, j = idx / rows;
+      const int c = order[j];
+      const float nv = norms[c];
+      Wg[r + int64_t(j) * ldw] = nv > 0.f ? W[r + c * ldW] / nv : 0.f;
+    }
+    for (int idx = tid; idx < cols * cols; idx += nt) {
+      const int r = idx % cols, j = idx / cols;
+      Vg[r + int64_t(j) * ldv] = V[r + order[j] * ldV];
+    }
+  } else {
+    // normalise in place, then permute by cycles using one column of scratch
+    // per step (done serially over columns; cols is small).
+    for (int idx = tid; idx < rows * cols; idx += nt) {
+      const int r = idx % rows, c = idx / rows;
+      const float nv = norms[c];
+      W[r + c * ldW] = nv > 0.f ? W[r + c * ldW] / nv : 0.f;
+    }
+    __syncthreads();
+    __shared__ int done[1024];
+    for (int c = tid; c < cols; c += nt) done[c] = 0;
+    __syncthreads();
+    for (int j = 0; j < cols; ++j) {
+      if (done[j] || order[j] == j) continue;
+      // cycle starting at j: dst j <- src order[j] <- ...
+      float tw = 0.f;  // each thread carries one element per row/col slot
+      // save column j of W and V
+      float savew[8], savev[8];
+      int cnt = 0;
+      for (int r = tid; r < rows; r += nt) savew[cnt++] = W[r + j * ldW];
+      cnt = 0;
+      for (int r = tid; r < cols; r += nt) savev[cnt++] = V[r + j * ldV];
+      __syncthreads();
+      int d = j;
+      while (true) {
+        const int src = order[d];
+        if (src == j) break;
+        for (int r = tid; r < rows; r += nt) W[r + d * ldW] = W[r + src * ldW];
+        for (int r = tid; r < cols; r += nt) V[r + d * ldV] = V[r + src * ldV];
+        __syncthreads();
+        if (tid == 0) done[d] = 1;
+        d = src;
+      }
+      cnt = 0;
+      for (int r = tid; r < rows; r += nt) W[r + d * ldW] = savew[cnt++];
+      cnt = 0;
+      for (int r = tid; r < cols; r += nt) V[r + d * ldV] = savev[cnt++];
+      if (tid == 0) done[d] = 1;
+      __syncthreads();
+      (void)tw;
+    }
+  }
+  for (int j = tid; j < cols; j += nt) {
+    S[j] = norms[order[j]];
+    if (S64) S64[j] = double(norms[order[j]]);
+  }
+}
+
+inline int grid_for(int64_t total) { return int(std::min<int64_t>(4096, std::max<int64_t>(1, (total + 255) / 256))); }
+
+}  // namespace
+
+void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  if (ld == rows) {
+    LR_CHECK_CUDA(cudaMemsetAsync(p, 0, size_t(rows) * cols * sizeof(float), s));
+  } else {
+    LR_CHECK_CUDA(cudaMemset2DAsync(p, size_t(ld) * sizeof(float), 0, size_t(rows) * sizeof(float), size_t(cols), s));
+  }
+}
+
+void zero_bytes(void* p, size_t bytes, cudaStream_t s) {
+  if (bytes) LR_CHECK_CUDA(cudaMemsetAsync(p, 0, bytes, s));
+}
+
+void f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, __nv_bfloat16* lo, int64_t ldd, int64_t rows,
+                 int64_t cols, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  f32_to_bf16_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, lo, ldd, rows, cols);
+  LR_LAUNCH_CHECK();
+}
+
+void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  copy_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+  LR_LAUNCH_CHECK();
+}
+
+void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n, int k, cudaStream_t s) {
+  if (k <= 0) return;
+  fix_signs_kernel<<<k, 256, 0, s>>>(U, ldu, m, V, ldv, n);
+  LR_LAUNCH_CHECK();
+}
+
+void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int shifted,
+              int* status, cudaStream_t s) {
+  LR_REQUIRE(ell >= 1 && ell <= 128, LR_ERR_UNSUPPORTED, "chol_inv: block width must be <= 128");
+  const size_t smem = size_t(3) * ell * ell * sizeof(float);
+  static bool attr[64] = {};
+  int dev = 0;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  if (!attr[dev & 63]) {
+    LR_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 128 * 128 * 4));
+    attr[dev & 63] = true;
+  }
+  chol_inv_kernel<<<1, 1024, smem, s>>>(G, ell, Rinv, ldr, Racc, ldacc, init_acc ? 1 : 0, shifted, status);
+  LR_LAUNCH_CHECK();
+}
+
+void tri_inv(const double* R, int ldr, int n, float* X, int ldx, int* status, cudaStream_t s) {
+  LR_REQUIRE(n >= 1 && n <= 128, LR_ERR_UNSUPPORTED, "tri_inv: n must be <= 128");
+  static bool attr[64] = {};
+  int dev = 0;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  if (!attr[dev & 63]) {
+    LR_CHECK_CUDA(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 128 * 128 * 4));
+    attr[dev & 63] = true;
+  }
+  tri_inv_kernel<<<1, 1024, size_t(2) * n * n * sizeof(float), s>>>(R, ldr, n, X, ldx, status);
+  LR_LAUNCH_CHECK();
+}
+
+void add_block_f64(double* R, int ldr, int r0, int c0, const double* C, int ldc, int rows, int cols, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  add_block_kernel<<<grid_for(int64_t(rows) * cols), 256, 0, s>>>(R, ldr, r0, c0, C, ldc, rows, cols);
+  LR_LAUNCH_CHECK();
+}
+
+void f64_to_f32(const double* src, int lds, float* dst, int ldd, int rows, int cols, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  f64_to_f32_kernel<<<grid_for(int64_t(rows) * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+  LR_LAUNCH_CHECK();
+}
+
+void r_to_f32(const double* R, int ldr, int n, float* out, int ldo, bool trans, cudaStream_t s) {
+  r_to_f32_kernel<<<grid_for(int64_t(n) * n), 256, 0, s>>>(R, ldr, n, out, ldo, trans ? 1 : 0);
+  LR_LAUNCH_CHECK();
+}
+
+void scale_cols_f32(float* A, int64_t lda, int64_t rows, int cols, const float* scale, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  scale_cols_kernel<<<grid_for(rows * cols), 256, 0, s>>>(A, lda, rows, cols, scale);
+  LR_LAUNCH_CHECK();
+}
+
+void jacobi_svd(const float* M, int ldm, int rows, int cols, float* Wk, int ldw, float* V, int ldv, float* S,
+                double* S64, int* status, cudaStream_t s) {
+  LR_REQUIRE(rows >= cols && cols >= 1 && cols <= 1024, LR_ERR_UNSUPPORTED, "jacobi_svd: need rows >= cols, cols <= 1024");
+  const size_t need = (size_t(rows) * cols + size_t(cols) * cols) * sizeof(float);
+  int dev = 0;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  const size_t cap = size_t(dev_info(dev).max_smem_optin) - 16 * 1024;
+  if (need <= cap) {
+    static bool attr[64] = {};
+    if (!attr[dev & 63]) {
+      LR_CHECK_CUDA(cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cap)));
+      attr[dev & 63] = true;
+    }
+    jacobi_kernel<true><<<1, 1024, need, s>>>(M, ldm, rows, cols, Wk, ldw, V, ldv, S, S64, status);
+  } else {
+    LR_REQUIRE(rows <= 8 * 1024 && cols <= 8 * 1024, LR_ERR_UNSUPPORTED, "jacobi_svd: too large");
+    jacobi_kernel<false><<<1, 1024, 0, s>>>(M, ldm, rows, cols, Wk, ldw, V, ldv, S, S64, status);
+  }
+  LR_LAUNCH_CHECK();
+}
+
+DevInfo dev_info(int device) {
+  static DevInfo cache[64];
+  DevInfo& d = cache[device & 63];
+  if (d.sms == 0) {
+    LR_CHECK_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, device));
+    LR_CHECK_CUDA(cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  }
+  return d;
+}
+
+}  // namespace lr

@@ -1,0 +1,422 @@
+// BF16 views of A on the 5th-generation tensor cores (tcgen05 + TMA).
+//
+// A view multiplies the m x n matrix A by a tall thin matrix (Alg. 2 lines 4
+// and 6, Alg. 7 line 3, Alg. 9 lines 4-5 of Bjarkason 2018):
+//   range view     Y = A X     (mode 0; output rows = rows of A, K = n)
+//   co-range view  Z = A^T W   (mode 1; output rows = cols of A, K = rows)
+// The path is HBM-bound for the widths the method uses (2 ell / sizeof(bf16)
+// flop per byte of A), so the kernel's job is to stream A exactly once at
+// full bandwidth while the tensor cores keep up:
+//   * persistent grid, one CTA per SM, stream-K split of the flattened
+//     (output tile, k-block) iteration space, so every SM gets the same
+//     number of A tiles;
+//   * warp 0 issues TMA loads of 128-byte-swizzled A tiles and thin-operand
+//     tiles into a STAGES-deep shared-memory ring (mbarrier full/empty);
+//   * warp 1 issues tcgen05.mma (M = 128, N = padded ell, K = 16) into a
+//     TMEM accumulator per 128-row strip; the same swizzled A tile serves as
+//     a K-major operand (range) or an MN-major operand (co-range, the
+//     transpose is free);
+//   * warps 2-5 drain TMEM (tcgen05.ld) and add the partial tile into the
+//     FP32 output with atomics (partial tiles exist only where stream-K
+//     ranges cut a tile, at most two per CTA).
+// Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the
+// kernel records LR_ERR_TIMEOUT, lets in-flight copies and MMAs finish,
+// frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lr {
+namespace {
+
+constexpr uint64_t kTimeoutNs = 2000000000ull;
+constexpr int kThreads = 192;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity.  Returns false when the
+// CTA is aborting (another role timed out) or this wait timed out.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kTimeoutNs) {
+      *abort_flag = 1;
+      set_status(status, LR_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// tcgen05 shared-memory matrix descriptor, 128-byte swizzle (sm_100 family):
+// start address >> 4 in bits 0-13, leading byte offset >> 4 in bits 16-29,
+// stride byte offset >> 4 in bits 32-45, descriptor version 1 at bit 46,
+// layout type 2 (SWIZZLE_128B) in bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = uint64_t((saddr & 0x3FFFFu) >> 4);
+  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;
+  d |= 2ull << 61;
+  return d;
+}
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), A major (bit 15: 0 K-major, 1 MN-major), B K-major,
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t(n) >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct ViewParams {
+  int64_t m_out;        // valid output rows
+  int ell;              // valid output columns
+  int kblocks;          // ceil(K / 64)
+  int64_t iters_total;  // tiles * kblocks
+  float* out;
+  int64_t ldo;
+  int* status;
+};
+
+template <int MODE, int NS, int NCOL, int STAGES>
+struct Cfg {
+  static constexpr uint32_t kABytes = NS * 16384u;       // NS strips of 128 x 64 bf16
+  static constexpr uint32_t kBBytes = NCOL * 128u;       // NCOL rows x 64 bf16
+  static constexpr uint32_t kStage = kABytes + kBBytes;  // multiple of 1024
+  static constexpr uint32_t kTmemCols = (NS * NCOL <= 32) ? 32 : (NS * NCOL <= 64) ? 64 : (NS * NCOL <= 128) ? 128
+                                        : (NS * NCOL <= 256) ? 256 : 512;
+  static constexpr size_t kSmem = size_t(STAGES) * kStage + 1024 + 256;
+  static_assert(NS * NCOL <= 512, "TMEM holds 512 FP32 columns");
+  static_assert(NCOL % 16 == 0 && NCOL >= 16 && NCOL <= 256, "M=128 MMA needs N % 16 == 0, N <= 256");
+};
+
+template <int MODE, int NS, int NCOL, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    view_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ViewParams p) {
+  using C = Cfg<MODE, NS, NCOL, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * C::kStage);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t G = gridDim.x;
+  const int64_t it_begin = p.iters_total * blockIdx.x / G;
+  const int64_t it_end = p.iters_total * (blockIdx.x + 1) / G;
+  const int kb_n = p.kblocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      uint32_t stage = 0, phase = 0;
+      for (int64_t it = it_begin; it < it_end; ++it) {
+        const int tile = int(it / kb_n);
+        const int kb = int(it % kb_n);
+        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.status)) break;
+        uint8_t* sa = smem + stage * C::kStage;
+        uint8_t* sb = sa + C::kABytes;
+        mbar_expect_tx(&full[stage], C::kStage);
+        if (MODE == 0) {
+#pragma unroll
+          for (int s = 0; s < NS; ++s) tma_load_2d(sa + s * 16384, &tmA, &full[stage], kb * 64, tile * 128 * NS + s * 128);
+        } else {
+#pragma unroll
+          for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              tma_load_2d(sa + s * 16384 + h * 8192, &tmA, &full[stage], tile * 128 * NS + s * 128 + h * 64, kb * 64);
+        }
+        tma_load_2d(sb, &tmB, &full[stage], kb * 64, 0);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (*abort_flag) {  // let copies already issued land before the CTA exits
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 10000000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t kIdesc = idesc_bf16(NCOL, MODE == 1);
+      uint32_t stage = 0, phase = 0, acc_phase = 0;
+      int64_t it = it_begin;
+      bool ok = true;
+      while (ok && it < it_end) {
+        const int tile = int(it / kb_n);
+        const int64_t seg_end = (it_end < int64_t(tile + 1) * kb_n) ? it_end : int64_t(tile + 1) * kb_n;
+        if (!mbar_wait(acc_empty, acc_phase ^ 1u, abort_flag, p.status)) break;
+        tc_fence_after();
+        bool first = true;
+        for (; it < seg_end; ++it) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(smem + stage * C::kStage);
+          const uint32_t b_base = a_base + C::kABytes;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t bdesc = sw128_desc(b_base + kk * 32, 16, 1024);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+              const uint64_t adesc = (MODE == 0) ? sw128_desc(a_base + s * 16384 + kk * 32, 16, 1024)
+                                                 : sw128_desc(a_base + s * 16384 + kk * 2048, 8192, 1024);
+              umma_bf16(tmem_base + uint32_t(s * NCOL), adesc, bdesc, kIdesc, (first && kk == 0) ? 0u : 1u);
+            }
+          }
+          first = false;
+          umma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(acc_full);
+        acc_phase ^= 1u;
+      }
+      // All MMAs issued by this thread must complete before TMEM is freed.
+      umma_commit(drain);
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else {
+    // Epilogue: warps 2..5 own TMEM lane quarters (warp % 4).
+    const int q = warp & 3;
+    uint32_t acc_phase = 0;
+    int64_t it = it_begin;
+    while (it < it_end) {
+      const int tile = int(it / kb_n);
+      const int64_t seg_end = (it_end < int64_t(tile + 1) * kb_n) ? it_end : int64_t(tile + 1) * kb_n;
+      if (!mbar_wait(acc_full, acc_phase, abort_flag, p.status)) break;
+      tc_fence_after();
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const int64_t row = int64_t(tile) * 128 * NS + s * 128 + q * 32 + lane;
+        const bool row_ok = row < p.m_out;
+        float* orow = p.out + row;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NCOL; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem_base + (uint32_t(q * 32) << 16) + uint32_t(s * NCOL + c0), v);
+          if (row_ok) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < p.ell) atomicAdd(orow + int64_t(c0 + j) * p.ldo, v[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      if (lane == 0) mbar_arrive(acc_empty);
+      acc_phase ^= 1u;
+      it = seg_end;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(C::kTmemCols));
+  }
+}
+
+// ------------------------------------------------------------------ host
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  });
+  LR_REQUIRE(fn != nullptr, LR_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  return fn;
+}
+
+// 2-D BF16 tensor map over a row-major (dim1 x dim0) array with row stride
+// ld elements, box (box0 x box1), 128-byte swizzle, zero fill out of bounds.
+CUtensorMap make_map_bf16(const void* base, int64_t dim0, int64_t dim1, int64_t ld, int box0, int box1) {
+  LR_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, LR_ERR_ALIGNMENT, "TMA base not 16-byte aligned");
+  LR_REQUIRE((ld * 2) % 16 == 0, LR_ERR_ALIGNMENT, "TMA row stride not a multiple of 16 bytes");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {cuuint64_t(dim0), cuuint64_t(dim1)};
+  cuuint64_t strides[1] = {cuuint64_t(ld * 2)};
+  cuuint32_t box[2] = {cuuint32_t(box0), cuuint32_t(box1)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  LR_REQUIRE(r == CUDA_SUCCESS, LR_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
+  return m;
+}
+
+template <int MODE, int NCOL>
+void launch_ncol(const CUtensorMap& ma, const CUtensorMap& mb, ViewParams p, int tiles, int sms, cudaStream_t s) {
+  constexpr int NS = 2;
+  constexpr int STAGES = (NCOL <= 128) ? 4 : 3;
+  using C = Cfg<MODE, NS, NCOL, STAGES>;
+  auto kern = view_bf16_kernel<MODE, NS, NCOL, STAGES>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  if (!attr_set[dev & 63]) {
+    LR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::kSmem)));
+    attr_set[dev & 63] = true;
+  }
+  p.iters_total = int64_t(tiles) * p.kblocks;
+  int grid = int(std::min<int64_t>(sms, p.iters_total));
+  if (grid <= 0) return;
+  kern<<<grid, kThreads, C::kSmem, s>>>(ma, mb, p);
+  LR_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+int view_bf16_ncol(int ell) {
+  return ell <= 32 ? 32 : ell <= 64 ? 64 : ell <= 128 ? 128 : 256;
+}
+
+void view_bf16(const ViewBf16Args& a, cudaStream_t s) {
+  LR_REQUIRE(a.ell >= 1 && a.ell <= 256, LR_ERR_UNSUPPORTED, "bf16 view handles ell <= 256 per call");
+  if (a.rows <= 0 || a.n <= 0) return;
+  const int sms = dev_info(a.device).sms;
+  const __nv_bfloat16* abase = a.A + a.row0 * a.lda;
+  ViewParams p{};
+  p.ell = a.ell;
+  p.out = a.out;
+  p.ldo = a.ldo;
+  p.status = a.status;
+  const int ncol = view_bf16_ncol(a.ell);
+  if (a.mode == 0) {
+    // Y[row0 : row0+rows] += A[row0 : row0+rows, :] X ; X col-major n x ell (ld ldb)
+    CUtensorMap ma = make_map_bf16(abase, a.n, a.rows, a.lda, 64, 128);
+    CUtensorMap mb = make_map_bf16(a.B, a.n, a.ell, a.ldb, 64, ncol);
+    p.m_out = a.rows;
+    p.kblocks = ceil_div(a.n, 64);
+    const int tiles = ceil_div(a.rows, 256);
+    switch (ncol) {
+      case 32: launch_ncol<0, 32>(ma, mb, p, tiles, sms, s); break;
+      case 64: launch_ncol<0, 64>(ma, mb, p, tiles, sms, s); break;
+      case 128: launch_ncol<0, 128>(ma, mb, p, tiles, sms, s); break;
+      default: launch_ncol<0, 256>(ma, mb, p, tiles, sms, s); break;
+    }
+  } else {
+    // Z += A[row0 : row0+rows, :]^T W_band ; W_band col-major (rows x ell,
+    // ld ldb) holds the operand rows of this band.
+    CUtensorMap ma = make_map_bf16(abase, a.n, a.rows, a.lda, 64, 64);
+    CUtensorMap mb = make_map_bf16(a.B, a.rows, a.ell, a.ldb, 64, ncol);
+    p.m_out = a.n;
+    p.kblocks = ceil_div(a.rows, 64);
+    const int tiles = ceil_div(a.n, 256);
+    switch (ncol) {
+      case 32: launch_ncol<1, 32>(ma, mb, p, tiles, sms, s); break;
+      case 64: launch_ncol<1, 64>(ma, mb, p, tiles, sms, s); break;
+      case 128: launch_ncol<1, 128>(ma, mb, p, tiles, sms, s); break;
+      default: launch_ncol<1, 256>(ma, mb, p, tiles, sms, s); break;
+    }
+  }
+}
+
+}  // namespace lr

@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP32 form, from the stated accuracy target): singular values
+max_i |s_i - s_i^oracle| / s_1^oracle <= 1e-5 and reconstruction error
+|e - e^oracle| / e^oracle <= 1e-5 with e = |A - U diag(s) V^T|_F in FP64;
+orthonormality |Q^T Q - I|_max <= 1e-5.  Views are compared with the FP64
+product of the same inputs (FP32 form) or of the BF16-rounded inputs (BF16
+form), relative Frobenius error <= 2e-5 (FP32 accumulation over K terms).
+Sizes span several tiles and ragged edges (rows, columns and widths that are
+not multiples of 128, 64 or 16).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import algorithms as Al  # noqa: E402
+from oracle import linalg as L  # noqa: E402
+from paper_1804_07531_gb300 import synth as S  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def api():
+    from paper_1804_07531_gb300 import api as _api
+    return _api
+
+
+def t32(x):
+    return torch.tensor(np.asarray(x, dtype=np.float32), device=DEV)
+
+
+def f64(t):
+    return t.detach().double().cpu().numpy()
+
+
+def rel_f(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_status_ok():
+    st = api().device_status(0)
+    assert st == 0, f"device status {st}"
+
+
+def check_tsvd(a64, u, s, v, uo, so, vo, tol=1e-5):
+    u, s, v = f64(u), f64(s), f64(v)
+    e_s = np.abs(s - so).max() / so[0]
+    e_g = Al.frob_error(a64, u, s, v)
+    e_o = Al.frob_error(a64, uo, so, vo)
+    d_e = abs(e_g - e_o) / e_o
+    k = s.shape[0]
+    orth_u = np.abs(u.T @ u - np.eye(k)).max()
+    orth_v = np.abs(v.T @ v - np.eye(k)).max()
+    msg = f"sigma {e_s:.2e} recon {d_e:.2e} orthU {orth_u:.2e} orthV {orth_v:.2e}"
+    assert e_s <= tol, msg
+    assert d_e <= tol, msg
+    assert orth_u <= tol and orth_v <= tol, msg
+    return msg
+
+
+# ---------------------------------------------------------------- views
+@pytest.mark.parametrize("m,n,ell", [(1000, 700, 30), (777, 1301, 1), (2048, 1024, 120), (515, 300, 250)])
+def test_views_fp32(m, n, ell):
+    a = S.gaussian(m, n, seed=m + n).astype(np.float32)
+    # rows padded to a 16-byte stride (the ABI's alignment rule), ragged n
+    ld = (n + 3) // 4 * 4
+    store = torch.zeros(m, ld, device=DEV)
+    store[:, :n] = t32(a)
+    at = store[:, :n]
+    x = S.gaussian(n, ell, seed=1).astype(np.float32)
+    w = S.gaussian(m, ell + 3, seed=2).astype(np.float32)
+    y, z = api().sketch(at, t32(x), t32(w))
+    assert_status_ok()
+    a64 = a.astype(np.float64)
+    assert rel_f(f64(y), a64 @ x) < 2e-5
+    assert rel_f(f64(z), a64.T @ w) < 2e-5
+    y1, _ = api().sketch(at, t32(x))
+    _, z1 = api().sketch(at, None, t32(w))
+    assert rel_f(f64(y1), a64 @ x) < 2e-5
+    assert rel_f(f64(z1), a64.T @ w) < 2e-5
+
+
+def _bf(x):
+    return torch.tensor(np.asarray(x, dtype=np.float32)).bfloat16()
+
+
+@pytest.mark.parametrize("m,n,ell", [(1000, 704, 30), (777, 1304, 1), (2048, 1024, 120), (520, 328, 250),
+                                     (4096, 2048, 64), (300, 512, 200)])
+def test_views_bf16_tensor_cores(m, n, ell):
+    a = _bf(S.gaussian(m, n, seed=m * 3 + n))
+    x = S.gaussian(n, ell, seed=3).astype(np.float32)
+    w = S.gaussian(m, ell, seed=4).astype(np.float32)
+    y, z = api().sketch(a.to(DEV), t32(x), t32(w))
+    assert_status_ok()
+    a64 = a.double().numpy()
+    xb = _bf(x).double().numpy()
+    wb = _bf(w).double().numpy()
+    ey, ez = rel_f(f64(y), a64 @ xb), rel_f(f64(z), a64.T @ wb)
+    assert ey < 2e-5 and ez < 2e-5, (ey, ez)
+    y1, _ = api().sketch(a.to(DEV), t32(x))
+    _, z1 = api().sketch(a.to(DEV), None, t32(w))
+    assert rel_f(f64(y1), a64 @ xb) < 2e-5
+    assert rel_f(f64(z1), a64.T @ wb) < 2e-5
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_chained_view(dtype):
+    m, n, ell = 3000, 1000, 40
+    a = S.gaussian(m, n, seed=5).astype(np.float32)
+    x = S.gaussian(n, ell, seed=6).astype(np.float32)
+    at = t32(a) if dtype == "f32" else _bf(a).to(DEV)
+    y, z = api().sketch_chained(at, t32(x))
+    assert_status_ok()
+    a64 = at.double().cpu().numpy()
+    xr = x.astype(np.float64) if dtype == "f32" else _bf(x).double().numpy()
+    y_ref = a64 @ xr
+    assert rel_f(f64(y), y_ref) < 2e-5
+    yr = f64(y) if dtype == "f32" else _bf(f64(y)).double().numpy()
+    assert rel_f(f64(z), a64.T @ yr) < 3e-5
+
+
+# ---------------------------------------------------------------- orth
+@pytest.mark.parametrize("m,ell", [(1000, 30), (4000, 120), (3000, 250), (700, 1), (5000, 300)])
+def test_orth_matches_householder(m, ell):
+    y = S.gaussian(m, ell, seed=m + ell).astype(np.float32)
+    y[:, 1:] += 0.5 * y[:, :1]            # correlated columns
+    q, r = api().orth(t32(y))
+    assert_status_ok()
+    qo, ro = L.householder_qr(y.astype(np.float64))
+    q64, r64 = f64(q), f64(r)
+    assert np.abs(q64.T @ q64 - np.eye(ell)).max() < 1e-5
+    assert rel_f(q64 @ r64, y.astype(np.float64)) < 1e-5
+    assert rel_f(r64, ro) < 1e-5
+    assert np.abs(q64 - qo).max() < 1e-4
+
+
+# ------------------------------------------------------------ algorithms
+@pytest.fixture(scope="module")
+def c1():
+    """Subspace-iteration workload: 2048 x 1024, sigma_j = 1/j, Haar U, V."""
+    cfg = S.CONFIGS["subspace_2048x1024_v3"]
+    a64 = S.usv(cfg["m"], cfg["n"], S.sigma_config("inv", cfg["n"]), cfg["seed_u"], cfg["seed_v"])
+    a32 = a64.astype(np.float32)
+    om = S.gaussian(cfg["n"], cfg["k"] + cfg["p"], seed=cfg["seed_omega"]).astype(np.float32)
+    return cfg, a32, om
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5])
+def test_subspace_iteration_parity(c1, v):
+    cfg, a32, om = c1
+    k, p = cfg["k"], cfg["p"]
+    a64 = a32.astype(np.float64)
+    u, s, vv = api().subspace_iter(t32(a32), k, p, v, t32(om))
+    assert_status_ok()
+    uo, so, vo = Al.gen_subspace_iteration(a64, om.astype(np.float64), k, v)
+    print(check_tsvd(a64, u, s, vv, uo, so, vo))
+
+
+@pytest.mark.parametrize("v", [2, 3, 4, 5])
+def test_block_krylov_parity(c1, v):
+    cfg, a32, om = c1
+    k, p = cfg["k"], cfg["p"]
+    a64 = a32.astype(np.float64)
+    u, s, vv = api().block_krylov(t32(a32), k, p, v, t32(om))
+    assert_status_ok()
+    uo, so, vo = Al.block_krylov(a64, om.astype(np.float64), k, v)
+    print(check_tsvd(a64, u, s, vv, uo, so, vo))
+
+
+@pytest.mark.parametrize("v", [2, 3, 4])
+def test_rowwise_block_krylov_parity(c1, v):
+    cfg, a32, om = c1
+    k, p = cfg["k"], cfg["p"]
+    a64 = a32.astype(np.float64)
+    u, s, vv = api().block_krylov(t32(a32), k, p, v, t32(om), enhanced=True)
+    assert_status_ok()
+    uo, so, vo = Al.rowwise_block_krylov(a64, om.astype(np.float64), k, v)
+    print(check_tsvd(a64, u, s, vv, uo, so, vo))
+
+
+def test_rowwise_single_pass_parity(c1):
+    cfg, a32, om = c1
+    k = cfg["k"]
+    a64 = a32.astype(np.float64)
+    u, s, vv = api().rowwise_single_pass(t32(a32), k, t32(om))
+    assert_status_ok()
+    uo, so, vo = Al.rowwise_qb_svd(a64, om.astype(np.float64), k)
+    print(check_tsvd(a64, u, s, vv, uo, so, vo))
+
+
+@pytest.mark.parametrize("l_c", [None, 10, 0])
+def test_single_pass_parity(l_c):
+    """Single-pass workload shape (scaled): low rank + noise, exp decay."""
+    m, n, k, ell1, ell2 = 3000, 1500, 20, 40, 80
+    a64 = S.usv(m, n, S.sigma_config("exp25", 256), 21, 22) + 1e-4 * S.gaussian(m, n, seed=23)
+    a32 = a64.astype(np.float32)
+    a64 = a32.astype(np.float64)
+    om = S.gaussian(n, ell1, seed=24).astype(np.float32)
+    ps = S.gaussian(m, ell2, seed=25).astype(np.float32)
+    u, s, vv = api().single_pass(t32(a32), k, t32(om), t32(ps), l_c=l_c)
+    assert_status_ok()
+    uo, so, vo = Al.single_pass(a64, om.astype(np.float64), ps.astype(np.float64), k, l_c=l_c)
+    print(check_tsvd(a64, u, s, vv, uo, so, vo))
+
+
+@pytest.mark.parametrize("algo", ["subspace", "krylov"])
+def test_bf16_form_matches_oracle_on_bf16_matrix(algo):
+    """BF16 form: A stored in BF16 is the matrix; operands rounded to BF16."""
+    m, n, k, p, v = 4096, 2048, 20, 10, 4
+    a64 = S.usv(m, n, S.sigma_config("pow15", n), 31, 32)
+    ab = torch.tensor(a64, dtype=torch.float32).bfloat16()
+    a_exact = ab.double().numpy()
+    om = S.gaussian(n, k + p, seed=33).astype(np.float32)
+    fn = api().subspace_iter if algo == "subspace" else api().block_krylov
+    u, s, vv = fn(ab.to(DEV), k, p, v, t32(om))
+    assert_status_ok()
+    ref = Al.gen_subspace_iteration if algo == "subspace" else Al.block_krylov
+    uo, so, vo = ref(a_exact, om.astype(np.float64), k, v)
+    e_g = Al.frob_error(a_exact, f64(u), f64(s), f64(vv))
+    e_o = Al.frob_error(a_exact, uo, so, vo)
+    # BF16 operands perturb the subspace slightly: error within 1% of FP64.
+    assert e_g <= 1.01 * e_o, (e_g, e_o)
+    assert np.abs(f64(s) - so).max() / so[0] < 1e-3
