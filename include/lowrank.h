@@ -194,6 +194,28 @@ lr_status lr_trace_read(lr_handle handle, int kind, double* total_ms, int64_t* l
 /* Number of CUDA kernels this process has launched through the library. */
 lr_status lr_kernel_launches(lr_handle handle, uint64_t* count);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free range view (the paper has no counterpart).
+ * ------------------------------------------------------------------- */
+
+/* Y = A X exactly as lr_sketch computes it with W = NULL, for callers that
+ * cannot call cudaMalloc at all -- e.g. a host program whose own pool has
+ * reserved the device's memory, or one that cannot accept the device-wide
+ * synchronisation a cudaMalloc may imply -- and therefore cannot create an
+ * lr_handle or provide a workspace.  No handle is needed and nothing is
+ * allocated: the BF16 copy of X that the tensor-core kernel reads lives in a
+ * 4 MiB file-scope device array (held on every GPU that loads the library
+ * until the library is unloaded), so ceil8(n) * ell * 2 bytes must fit in
+ * 4 MiB minus 256 bytes (else LR_ERR_UNSUPPORTED), and ell <= 256.  An F32 A
+ * needs no scratch.  Arguments as for lr_sketch; runs on the current device
+ * and `stream`.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins.  All calls share the array: calls that overlap on the GPU
+ * (other streams or host threads on the same device) race and must be
+ * serialised by the caller.  Device-side timeouts are not reported (there is
+ * no handle to hold a status); argument errors are returned synchronously. */
+lr_status lr_sketch_range_static(const lr_mat* A, const lr_mat* X, lr_mat* Y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
