@@ -318,14 +318,18 @@ void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
 }
 
 // --------------------------------------------------------- core SVD
-// R (n x n upper, FP64) = W diag(S) Vj^T, all outputs FP32 n x n.
-void core_svd(Ctx& c, const double* R, int n, float* W, float* Vj, float* S) {
+// R (n x n upper, FP64) = Left diag(S) Right^T, outputs FP32 n x n.
+// One-sided Jacobi runs on R^T: the rows of R are graded for the bases
+// built here (earlier Krylov/subspace directions carry larger norms), which
+// makes the columns of R^T converge in fewer sweeps.  R^T = Um S Vm^T gives
+// Left = Vm (accumulated rotations) and Right = Um (normalised columns).
+void core_svd(Ctx& c, const double* R, int n, float* Left, float* Right, float* S) {
   ArenaScope sc(c.ar);
   float* M = c.ar.take<float>(size_t(n) * n);
   if (c.measure) return;
   TraceScope tr(c, LR_TRACE_CORE_SVD);
-  r_to_f32(R, n, n, M, n, false, c.s);
-  jacobi_svd(M, n, n, n, W, n, Vj, n, S, nullptr, c.status, c.s);
+  r_to_f32(R, n, n, M, n, true, c.s);
+  jacobi_svd(M, n, n, n, Right, n, Left, n, S, nullptr, c.status, c.s);
 }
 
 struct Outs {

@@ -157,11 +157,14 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict
     const float ljj = L[j + j * n];
     for (int i = j + 1 + tid; i < n; i += nt) L[i + j * n] /= ljj;
     __syncthreads();
-    // trailing update of the lower triangle: L(i,c) -= L(i,j) L(c,j), j < c <= i
-    const int m = n - j - 1;
-    for (int idx = tid; idx < m * m; idx += nt) {
-      const int c = j + 1 + idx / m, i = j + 1 + idx % m;
-      if (i >= c) L[i + c * n] -= L[i + j * n] * L[c + j * n];
+    // trailing update of the lower triangle, L(i,c) -= L(i,j) L(c,j) for
+    // j < c <= i; 32 x 32 thread grid: ty walks columns, tx walks rows
+    {
+      const int tx = tid & 31, ty = tid >> 5;
+      for (int c = j + 1 + ty; c < n; c += 32) {
+        const float lcj = L[c + j * n];
+        for (int i = c + tx; i < n; i += 32) L[i + c * n] -= L[i + j * n] * lcj;
+      }
     }
     __syncthreads();
   }
@@ -199,13 +202,14 @@ __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict
         L[idx] = (r <= c) ? float(Racc[r + c * ldacc]) : 0.f;
       }
       __syncthreads();
-      for (int idx = tid; idx < n * n; idx += nt) {
-        const int r = idx % n, c = idx / n;
-        float acc = 0.f;
-        if (r <= c)
-          for (int k = r; k <= c; ++k) acc = fmaf(T[r + k * n], L[k + c * n], acc);
-        Racc[r + c * ldacc] = double(acc);
-      }
+      const int tx = tid & 31, ty = tid >> 5;
+      for (int c = ty; c < n; c += 32)
+        for (int r = tx; r < n; r += 32) {
+          float acc = 0.f;
+          if (r <= c)
+            for (int k = r; k <= c; ++k) acc = fmaf(T[r + k * n], L[k + c * n], acc);
+          Racc[r + c * ldacc] = double(acc);
+        }
     }
   }
 }
@@ -533,6 +537,11 @@ void jacobi_svd(const float* M, int ldm, int rows, int cols, float* Wk, int ldw,
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   const size_t cap = size_t(dev_info(dev).max_smem_optin) - 16 * 1024;
+  // square cores wider than one SM comfortably holds: rows split over a cluster
+  if (rows == cols && S64 == nullptr && jacobi_cluster_size(cols) > 0) {
+    jacobi_svd_cluster(M, ldm, cols, Wk, ldw, V, ldv, S, status, s);
+    return;
+  }
   if (need <= cap) {
     static bool attr[64] = {};
     if (!attr[dev & 63]) {

@@ -49,6 +49,22 @@ def haar(n: int, r: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(q * d[None, :])
 
 
+def _preload_torch_linalg():
+    """Load torch's CUDA linear-algebra library by path so that torch's own
+    lazy dlopen of it succeeds in environments (profilers) that alter the
+    library search path."""
+    import ctypes
+    import glob
+    import os
+
+    import torch
+    for lib in glob.glob(os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so*")):
+        try:
+            ctypes.CDLL(lib, mode=ctypes.RTLD_GLOBAL)
+        except OSError:
+            pass
+
+
 def haar_torch(n: int, r: int, seed: int, device="cuda", dtype=None):
     """Haar columns built with torch on `device` (fixture for large shapes).
 
@@ -58,6 +74,7 @@ def haar_torch(n: int, r: int, seed: int, device="cuda", dtype=None):
     """
     import torch
 
+    _preload_torch_linalg()
     dtype = dtype or torch.float32
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
