@@ -17,7 +17,7 @@ from ._binding import (Handle, LowrankError, LrMat, _opts, _stream, col_major, e
 
 __all__ = [
     "sketch", "sketch_chained", "orth", "subspace_iter", "single_pass", "block_krylov",
-    "rowwise_single_pass", "device_status", "LowrankError",
+    "rowwise_single_pass", "subspace_iter_backward", "device_status", "LowrankError",
 ]
 
 
@@ -156,3 +156,18 @@ def device_status(device=None, stream=None) -> int:
     """Read and clear the device status word (synchronises the stream)."""
     h = Handle.get(device if device is not None else torch.cuda.current_device())
     return h.status(stream)
+
+
+def subspace_iter_backward(a, k, p, v, omega, ds, stream=None):
+    """dA for L = sum_i ds_i sigma_i of Alg. 2 (views recomputed, dA written once)."""
+    a, (omega,) = _prep(a, omega)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    h.reserve(m, n, k + p, 0, v)
+    ds = ds.detach().to(device=a.device, dtype=torch.float32).contiguous()
+    da = torch.empty(m, n, device=a.device, dtype=torch.float32)
+    mats = [mat_a(a), mat_thin(omega), mat_thin(ds), mat_a(da)]
+    o = _opts()
+    _call(h, lib().lr_subspace_iter_backward, _p(mats[0]), k, p, v, _p(mats[1]), _p(mats[2]), _p(mats[3]),
+          ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return da

@@ -98,9 +98,10 @@ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 // ----------------------------------------------------------- thin GEMMs
 // C (M x N) = alpha op(A) op(B) + beta C, all FP32 column-major.
 void gemm(Ctx& c, int64_t M, int64_t N, int64_t K, bool ta, const float* A, int64_t lda, bool tb, const float* B,
-          int64_t ldb, float* C, int64_t ldc, float alpha = 1.f, float beta = 0.f) {
+          int64_t ldb, float* C, int64_t ldc, float alpha = 1.f, float beta = 0.f, const int* run_if = nullptr) {
   if (c.measure) return;
   GemmArgs g;
+  g.run_if = run_if;
   g.M = M; g.N = N; g.K = K; g.ta = ta; g.tb = tb; g.alpha = alpha; g.beta = beta;
   g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C = C; g.ldc = ldc;
   g.mode = GEMM_STORE;
@@ -110,7 +111,7 @@ void gemm(Ctx& c, int64_t M, int64_t N, int64_t K, bool ta, const float* A, int6
 // C64 (M x N, ld ldc) = op(A)^T-style reduction over a long K with FP32
 // products and FP64 accumulation across K slices (Grams, cross-Grams).
 void gram64(Ctx& c, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
-            double* C64, int64_t ldc) {
+            double* C64, int64_t ldc, const int* run_if = nullptr) {
   if (c.measure) return;
   LR_CHECK_CUDA(cudaMemsetAsync(C64, 0, size_t(ldc) * N * sizeof(double), c.s));
   GemmArgs g;
@@ -118,6 +119,7 @@ void gram64(Ctx& c, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
   g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.C64 = C64; g.ldc = ldc;
   g.mode = GEMM_ATOMIC_F64;
   g.split_k = split_for(M, N, K, c.sms);
+  g.run_if = run_if;
   sgemm(g, c.s);
 }
 
@@ -277,21 +279,17 @@ void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
   double* G64 = c.ar.take<double>(size_t(std::max(L, wmax)) * wmax);
   float* C32 = c.ar.take<float>(size_t(L) * wmax);
   float* Rinv = c.ar.take<float>(size_t(wmax) * wmax);
+  int* flags = c.ar.take<int>(size_t(nb));
   if (c.measure) return;
   TraceScope tr(c, LR_TRACE_ORTH);
   if (R) LR_CHECK_CUDA(cudaMemsetAsync(R, 0, size_t(L) * L * sizeof(double), c.s));
-  // Shifted CholeskyQR3 (Fukaya et al. 2020): with FP32 Cholesky, plain
-  // CholeskyQR2 breaks down once kappa(Y) nears 1e3, which sketches of
-  // steep spectra and Krylov bases reach, so every block takes one shifted
-  // pass followed by two unshifted ones.  `robust` is kept for callers that
-  // know their input is ill-conditioned; it no longer changes the passes.
+  LR_CHECK_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * nb, c.s));
   (void)robust;
-  const bool shifted = true;
-  const int passes = 3;
   int c0 = 0;
   for (int b = 0; b < nb; ++b) {
     const int w = L / nb + (b < L % nb ? 1 : 0);
     float* Yb = Y.col(c0);
+    int* more = flags + b;
     if (c0 > 0) {
       for (int pass = 0; pass < 2; ++pass) {
         gram64(c, c0, w, m, Y.p, Y.ld, Yb, Y.ld, G64, c0);          // C = Q_prev^T Y_b
@@ -300,19 +298,25 @@ void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
         if (R) add_block_f64(R, L, 0, c0, G64, c0, c0, w, c.s);
       }
     }
-    // CholeskyQR passes ping-pong between Y_b and T; R_bb = R_last ... R_1.
-    bool in_t = false;
-    for (int pass = 0; pass < passes; ++pass) {
-      float* src = in_t ? T : Yb;
-      float* dst = in_t ? Yb : T;
-      const int64_t lds = in_t ? m : Y.ld, ldd = in_t ? Y.ld : m;
-      gram64(c, w, w, m, src, lds, src, lds, G64, w);
-      chol_inv(G64, w, Rinv, w, R ? R + c0 + int64_t(c0) * L : nullptr, L, pass == 0,
-               (shifted && pass == 0) ? 1 : 0, c.status, c.s);
-      gemm(c, m, w, w, false, src, lds, false, Rinv, w, dst, ldd);
-      in_t = !in_t;
-    }
-    if (in_t) copy_f32(T, m, Yb, Y.ld, m, w, c.s);
+    // CholeskyQR2 with a breakdown-triggered shift (shifted CholeskyQR3,
+    // Fukaya et al. 2020): pass 1 is plain, or shifted when the plain
+    // Cholesky breaks down -- which happens in FP32 once kappa(Y_b) nears
+    // 1e3 -- and then flags a third pass that the device runs only if set.
+    // Passes alternate Y_b -> T -> Y_b -> T; R_bb = R_last ... R_1.
+    double* Rbb = R ? R + c0 + int64_t(c0) * L : nullptr;
+    // pass 1: Y_b -> T
+    gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w);
+    chol_inv(G64, w, Rinv, w, Rbb, L, true, CHOL_SHIFT_IF_NEEDED, more, c.status, c.s);
+    gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m);
+    // pass 2: T -> Y_b
+    gram64(c, w, w, m, T, m, T, m, G64, w);
+    chol_inv(G64, w, Rinv, w, Rbb, L, false, CHOL_PLAIN, more, c.status, c.s);
+    gemm(c, m, w, w, false, T, m, false, Rinv, w, Yb, Y.ld);
+    // pass 3 (only after a shifted pass 1): Y_b -> T -> Y_b
+    gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w, more);
+    chol_inv(G64, w, Rinv, w, Rbb, L, false, CHOL_IF_FLAGGED, more, c.status, c.s);
+    gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m, 1.f, 0.f, more);
+    copy_f32(T, m, Yb, Y.ld, m, w, c.s, more);
     c0 += w;
   }
 }
@@ -521,6 +525,98 @@ void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const
   write_outputs(c, Qc, Vj, Xt, W, Lc, Sv, k, o);
 }
 
+// ------------------------------------------------- reverse of Alg. 2
+// dA for L = sum_i dS_i sigma_i(R) where R is the last view's triangular
+// factor (the core of Alg. 2).  The forward views are recomputed (nothing is
+// kept from lr_subspace_iter).  Reverse rules (standard matrix calculus,
+// the paper has no derivatives):
+//   core:  R = W S Z^T  ->  Rb = W_k diag(dS) Z_k^T;
+//   thin QR B = Q R:  M = R Rb^T - Qb^T Q, Bb = (Qb + Q copyltu(M)) R^{-T};
+//   view B = A X:  dA += Bb X^T, Xb = A^T Bb;  B = A^T X:  dA += X Bb^T, Xb = A Bb.
+// Every dA term is an outer product of two ell-column panels, so dA is
+// written once by one GEMM: dA = [L_1 .. L_v] [R_1 .. R_v]^T with
+// (L_j, R_j) = (Bb_j, X_j) for odd j and (X_j, Bb_j) for even j.
+void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, const float* dS, float* dA,
+                           int64_t ldda) {
+  ArenaScope sc(c.ar);
+  const int64_t m = A.m, n = A.n;
+  Mat Lc{c.ar.take<float>(size_t(m) * v * ell), m, int64_t(v) * ell, m};   // m-side panels
+  Mat Rc{c.ar.take<float>(size_t(n) * v * ell), n, int64_t(v) * ell, n};   // n-side panels
+  const int64_t rows_v = (v % 2 == 1) ? m : n;
+  Mat Qv{c.ar.take<float>(size_t(rows_v) * ell), rows_v, ell, rows_v};      // Q of the last view
+  double* Rs = c.ar.take<double>(size_t(v) * ell * ell);
+  float* W = c.ar.take<float>(size_t(ell) * ell);
+  float* Z = c.ar.take<float>(size_t(ell) * ell);
+  float* Sv = c.ar.take<float>(size_t(ell));
+  float* Rb = c.ar.take<float>(size_t(ell) * ell);
+  float* Rf = c.ar.take<float>(size_t(ell) * ell);
+  float* Mm = c.ar.take<float>(size_t(ell) * ell);
+  float* Ms = c.ar.take<float>(size_t(ell) * ell);
+  float* Ri = c.ar.take<float>(size_t(ell) * ell);
+  double* C64 = c.ar.take<double>(size_t(ell) * ell);
+  const int64_t mx = std::max(m, n);
+  float* rhs = c.ar.take<float>(size_t(mx) * ell);
+  float* Qb = c.ar.take<float>(size_t(mx) * ell);
+  float* dSd = c.ar.take<float>(size_t(ell));
+  // slot j (1-based) of the panel lists; Q_j of view j lands in the slot of
+  // view j + 1 (odd j: Lc, even j: Rc), Omega in Rc slot 1
+  auto lslot = [&](int j) { return Mat{Lc.col(int64_t(j - 1) * ell), m, ell, m}; };
+  auto rslot = [&](int j) { return Mat{Rc.col(int64_t(j - 1) * ell), n, ell, n}; };
+  if (c.measure) {  // account for the helpers' own temporaries
+    orth(c, Mat{nullptr, mx, ell, mx}, nullptr);
+    core_svd(c, nullptr, ell, nullptr, nullptr, nullptr);
+    return;
+  }
+  copy_f32(Om.p, Om.ld, rslot(1).p, n, n, ell, c.s);
+  // ---- forward recomputation: B_j = A Q_{j-1} (odd) or A^T Q_{j-1} (even)
+  for (int j = 1; j <= v; ++j) {
+    const bool odd = j % 2 == 1;
+    Mat in = odd ? rslot(j) : lslot(j);
+    Mat out = (j == v) ? Qv : (odd ? lslot(j + 1) : rslot(j + 1));
+    if (odd) view_range(c, A, in, out);
+    else view_corange(c, A, in, out);
+    orth(c, out, Rs + size_t(j - 1) * ell * ell);
+  }
+  // ---- core: R_v = W S Z^T, Rb = W_k diag(dS) Z_k^T
+  core_svd(c, Rs + size_t(v - 1) * ell * ell, ell, W, Z, Sv);
+  LR_CHECK_CUDA(cudaMemcpyAsync(dSd, dS, sizeof(float) * k, cudaMemcpyDeviceToDevice, c.s));
+  scale_cols_f32(W, ell, ell, k, dSd, c.s);
+  gemm(c, ell, ell, k, false, W, ell, true, Z, ell, Rb, ell);
+  // ---- reverse through the views
+  bool have_qb = false;
+  for (int j = v; j >= 1; --j) {
+    const bool odd = j % 2 == 1;
+    const int64_t rows = odd ? m : n;
+    Mat Q = (j == v) ? Qv : (odd ? lslot(j + 1) : rslot(j + 1));
+    const double* R = Rs + size_t(j - 1) * ell * ell;
+    // M = R Rb^T - Qb^T Q  (Rb = 0 below the last view)
+    if (j == v) {
+      r_to_f32(R, ell, ell, Rf, ell, false, c.s);
+      gemm(c, ell, ell, ell, false, Rf, ell, true, Rb, ell, Mm, ell);
+    } else {
+      LR_CHECK_CUDA(cudaMemsetAsync(Mm, 0, sizeof(float) * ell * ell, c.s));
+    }
+    if (have_qb) gram64(c, ell, ell, rows, Qb, rows, Q.p, Q.ld, C64, ell);
+    qr_bwd_sym(Mm, have_qb ? C64 : nullptr, ell, Ms, c.s);
+    // rhs = Qb + Q copyltu(M)
+    if (have_qb) copy_f32(Qb, rows, rhs, rows, rows, ell, c.s);
+    gemm(c, rows, ell, ell, false, Q.p, Q.ld, false, Ms, ell, rhs, rows, 1.f, have_qb ? 1.f : 0.f);
+    // Bb = rhs R^{-T}, written into this view's panel slot
+    tri_inv(R, ell, ell, Ri, ell, c.status, c.s);
+    Mat Bb = odd ? lslot(j) : rslot(j);
+    gemm(c, rows, ell, ell, false, rhs, rows, true, Ri, ell, Bb.p, Bb.ld);
+    if (j > 1) {
+      // Qb_{j-1} = A^T Bb (odd j) or A Bb (even j)
+      Mat qb{Qb, odd ? n : m, ell, odd ? n : m};
+      if (odd) view_corange(c, A, Bb, qb);
+      else view_range(c, A, Bb, qb);
+      have_qb = true;
+    }
+  }
+  // ---- dA = Lc Rc^T, one GEMM (as column-major: dA^T = Rc Lc^T)
+  gemm(c, n, m, int64_t(v) * ell, false, Rc.p, Rc.ld, true, Lc.p, Lc.ld, dA, ldda);
+}
+
 // ------------------------------------------------------- validation
 AMat check_A(const lr_mat* A) {
   LR_REQUIRE(A && A->data, LR_ERR_INVALID_ARG, "A is NULL");
@@ -703,6 +799,8 @@ lr_status lr_workspace_size(lr_handle h, int64_t m, int64_t n, int ell1, int ell
         measure([&](Ctx& c) { run_krylov_rowwise(c, A, k, ell1, vv, Om, o); });
         measure([&](Ctx& c) { run_rowwise_qb(c, A, k, ell1, Om, o); });
       }
+      if (!A.bf16 && ell1 <= kMaxBlock)
+        measure([&](Ctx& c) { run_subspace_backward(c, A, 1, ell1, vv, Om, nullptr, nullptr, 0); });
       if (ell2 >= ell1) {
         Mat Ps{nullptr, m, ell2, m};
         measure([&](Ctx& c) { run_single_pass(c, A, std::max(1, ell1 - 1), -1, Om, Ps, o); });
@@ -837,9 +935,23 @@ lr_status lr_single_pass_host(lr_handle h, const lr_mat*, int64_t, int, const lr
   return guarded(h, [&] { throw Error{LR_ERR_UNSUPPORTED, "host-streamed single pass is not built yet"}; });
 }
 
-lr_status lr_subspace_iter_backward(lr_handle h, const lr_mat*, int, int, int, const lr_mat*, const lr_mat*, lr_mat*,
-                                    const lr_opts*, void*) {
-  return guarded(h, [&] { throw Error{LR_ERR_UNSUPPORTED, "backward is not built yet"}; });
+lr_status lr_subspace_iter_backward(lr_handle h, const lr_mat* A, int k, int p, int v, const lr_mat* Omega,
+                                    const lr_mat* dS, lr_mat* dA, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    LR_REQUIRE(!a.bf16, LR_ERR_DTYPE, "the reverse pass needs an F32 A");
+    check_kpv(a, k, p, v, 2);
+    LR_REQUIRE(k + p <= kMaxBlock, LR_ERR_UNSUPPORTED, "the reverse pass needs k + p <= 128");
+    Mat om = check_thin(Omega, a.n, k + p, "Omega");
+    LR_REQUIRE(dS && dS->data && dS->dtype == LR_F32 && dS->rows * dS->cols >= k, LR_ERR_SHAPE,
+               "dS must hold k F32 weights");
+    LR_REQUIRE(dA && dA->data && dA->dtype == LR_F32 && dA->col_major == 0 && dA->rows == a.m && dA->cols == a.n &&
+                   dA->ld >= a.n,
+               LR_ERR_SHAPE, "dA must be an F32 row-major m x n matrix");
+    Ctx c = make_ctx(h, opts, stream);
+    run_subspace_backward(c, a, k, k + p, v, om, static_cast<const float*>(dS->data), static_cast<float*>(dA->data),
+                          dA->ld);
+  });
 }
 
 lr_status lr_set_trace(lr_handle h, int on) {

@@ -30,7 +30,9 @@ template <bool TA, bool TB, int BM, int BN, int MODE>
 __global__ void __launch_bounds__(NT) sgemm_kernel(int M, int N, int K, int kchunk, float alpha,
                                                    const float* __restrict__ A, int64_t lda,
                                                    const float* __restrict__ B, int64_t ldb,
-                                                   float beta, float* C, double* C64, int64_t ldc) {
+                                                   float beta, float* C, double* C64, int64_t ldc,
+                                                   const int* run_if) {
+  if (run_if && *run_if == 0) return;
   constexpr int TM = BM / 16;  // rows per thread
   constexpr int TN = BN / 16;  // cols per thread
   __shared__ float As[BK][BM + 4];
@@ -125,15 +127,15 @@ void launch_t(const GemmArgs& g, cudaStream_t s) {
   switch (g.mode) {
     case GEMM_STORE:
       sgemm_kernel<TA, TB, BM, BN, GEMM_STORE><<<grid, NT, 0, s>>>(
-          g.M, g.N, g.K, kchunk, g.alpha, g.A, g.lda, g.B, g.ldb, g.beta, g.C, g.C64, g.ldc);
+          g.M, g.N, g.K, kchunk, g.alpha, g.A, g.lda, g.B, g.ldb, g.beta, g.C, g.C64, g.ldc, g.run_if);
       break;
     case GEMM_ATOMIC_F32:
       sgemm_kernel<TA, TB, BM, BN, GEMM_ATOMIC_F32><<<grid, NT, 0, s>>>(
-          g.M, g.N, g.K, kchunk, g.alpha, g.A, g.lda, g.B, g.ldb, g.beta, g.C, g.C64, g.ldc);
+          g.M, g.N, g.K, kchunk, g.alpha, g.A, g.lda, g.B, g.ldb, g.beta, g.C, g.C64, g.ldc, g.run_if);
       break;
     default:
       sgemm_kernel<TA, TB, BM, BN, GEMM_ATOMIC_F64><<<grid, NT, 0, s>>>(
-          g.M, g.N, g.K, kchunk, g.alpha, g.A, g.lda, g.B, g.ldb, g.beta, g.C, g.C64, g.ldc);
+          g.M, g.N, g.K, kchunk, g.alpha, g.A, g.lda, g.B, g.ldb, g.beta, g.C, g.C64, g.ldc, g.run_if);
       break;
   }
   LR_LAUNCH_CHECK();

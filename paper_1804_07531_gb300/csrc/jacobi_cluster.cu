@@ -69,11 +69,13 @@ __global__ void __launch_bounds__(kThreads) jacobi_cluster_kernel(const float* _
     V[idx] = (r < nr && r0 + r == c) ? 1.f : 0.f;
   }
   const float tol = 1.2e-7f * sqrtf(float(n));
+  const float tol2 = tol * tol;
   __syncthreads();
 
   int sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) rotated = 0;
+    __syncthreads();
     for (int rnd = 0; rnd < np - 1; ++rnd) {
       float* pb = part + (rnd & 1) * 3 * npairs;
       // circle method: position 0 fixed, the others rotate by one per round
@@ -111,14 +113,15 @@ __global__ void __launch_bounds__(kThreads) jacobi_cluster_kernel(const float* _
         pb[3 * pi + 2] = ga;
       }
       // 2. every CTA's partials are visible cluster-wide
-      cl.sync();
+      if (P > 1) cl.sync();
+      else __syncthreads();
       // 3. identical sums in every CTA (ranks in order), then local rotation
       // lane gl of the group sums ranks gl, gl + G, ... ; the group then sums
       // its lanes 0, 1, ... -- the same order in every CTA
       float ta = 0.f, tb = 0.f, tg = 0.f;
       if (live)
         for (int k = gl; k < P; k += G) {
-          const float* rp = cl.map_shared_rank(pb, k);
+          const float* rp = (P > 1) ? cl.map_shared_rank(pb, k) : pb;
           ta += rp[3 * pi];
           tb += rp[3 * pi + 1];
           tg += rp[3 * pi + 2];
@@ -132,10 +135,14 @@ __global__ void __launch_bounds__(kThreads) jacobi_cluster_kernel(const float* _
         be += __shfl_sync(0xffffffffu, tb, gbase + k);
         ga += __shfl_sync(0xffffffffu, tg, gbase + k);
       }
-      if (live && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
-        const float zeta = (be - al) / (2.f * ga);
-        const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-        const float c = 1.f / sqrtf(1.f + t * t);
+      // |gamma| > tol sqrt(alpha beta), tested without square roots
+      if (live && al > 0.f && be > 0.f && ga * ga > tol2 * al * be) {
+        // The angle only needs to be close; orthogonality of the rotation
+        // comes from c = rsqrt_rn(1 + t^2), s = c t (c^2 + s^2 = 1 to an
+        // ulp for any t), so t uses the fast division and square root.
+        const float zeta = __fdividef(be - al, 2.f * ga);
+        const float t = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+        const float c = __frsqrt_rn(fmaf(t, t, 1.f));
         const float s = c * t;
         float* wp = W + p * rpc;
         float* wq = W + q * rpc;
@@ -153,6 +160,8 @@ __global__ void __launch_bounds__(kThreads) jacobi_cluster_kernel(const float* _
       }
       __syncthreads();
     }
+    // converged once no pair needed a rotation (the same decision in every
+    // CTA of the cluster)
     if (!rotated) break;
     __syncthreads();
   }
@@ -183,7 +192,7 @@ __global__ void __launch_bounds__(kThreads) jacobi_cluster_kernel(const float* _
   for (int c = tid; c < n; c += kThreads) {
     float sw = 0.f, sv = 0.f;
     for (int k = 0; k < P; ++k) {
-      const float* rp = cl.map_shared_rank(pn, k);
+      const float* rp = (P > 1) ? cl.map_shared_rank(pn, k) : pn;
       sw += rp[c];
       sv += rp[n + c];
     }
@@ -225,6 +234,8 @@ size_t cluster_smem(int n, int P) {
 
 // Cluster size for an n x n core (0: does not fit a cluster of <= 8).
 int jacobi_cluster_size(int n) {
+  // Smallest cluster whose CTAs hold their rows of W and V (wider clusters
+  // pay more for the per-round cluster barrier than they save in work).
   for (int P = 1; P <= 8; P *= 2)
     if (cluster_smem(n, P) <= size_t(200) * 1024) return P;
   return 0;

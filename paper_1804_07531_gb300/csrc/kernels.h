@@ -22,6 +22,7 @@ struct GemmArgs {
   int64_t ldc = 0;
   int mode = GEMM_STORE;
   int split_k = 1;
+  const int* run_if = nullptr;  // device flag: the launch is a no-op when *run_if == 0
 };
 void sgemm(const GemmArgs& g, cudaStream_t s);
 int split_for(int64_t M, int64_t N, int64_t K, int sms);
@@ -49,7 +50,9 @@ void zero_bytes(void* p, size_t bytes, cudaStream_t s);
 // also lo = round(src - hi) (the hi/lo split of a thin operand).
 void f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, __nv_bfloat16* lo, int64_t ldd, int64_t rows,
                  int64_t cols, cudaStream_t s);
-void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s);
+// run_if (device int, optional): skip the copy when *run_if == 0.
+void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
+              const int* run_if = nullptr);
 // dst row-major = src^T for an F32 col-major src (rows x cols) -> (cols x rows)
 void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n, int k, cudaStream_t s);
 
@@ -58,8 +61,9 @@ void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t 
 //   G (ell x ell, FP64 col-major, ld ell) = R^T R; writes Rinv (FP32,
 //   ell x ell, ldr); Racc (FP64, ldacc) <- R (init_acc) or R * Racc.
 //   Racc may be nullptr.  Breakdown / non-finite -> status.
-void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int shifted,
-              int* status, cudaStream_t s);
+enum CholMode { CHOL_PLAIN = 0, CHOL_SHIFT_IF_NEEDED = 1, CHOL_IF_FLAGGED = 2 };
+void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int mode,
+              int* needs_more, int* status, cudaStream_t s);
 // X = R^{-1} (FP32) for an upper-triangular FP64 R (n <= 128).
 void tri_inv(const double* R, int ldr, int n, float* X, int ldx, int* status, cudaStream_t s);
 // R (ell x ell FP64) block (rows r0.., cols c0..) += C (FP64 in, col-major)
@@ -78,5 +82,7 @@ void jacobi_svd_cluster(const float* M, int ldm, int n, float* U, int ldu, float
 void r_to_f32(const double* R, int ldr, int n, float* out, int ldo, bool trans, cudaStream_t s);
 // Small dense QR helper for the single-pass core: see single_pass driver.
 void scale_cols_f32(float* A, int64_t lda, int64_t rows, int cols, const float* scale, cudaStream_t s);
+// out = copyltu(M - C): symmetric n x n from the lower triangle (C FP64 or null).
+void qr_bwd_sym(const float* M, const double* C, int n, float* out, cudaStream_t s);
 
 }  // namespace lr

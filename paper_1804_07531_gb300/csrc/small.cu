@@ -36,7 +36,8 @@ __global__ void f32_to_bf16_kernel(const float* __restrict__ src, int64_t lds, _
 }
 
 __global__ void copy_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ dst, int64_t ldd,
-                            int64_t rows, int64_t cols) {
+                            int64_t rows, int64_t cols, const int* run_if) {
+  if (run_if && *run_if == 0) return;
   int64_t total = rows * cols;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     int64_t r = i % rows, c = i / rows;
@@ -118,58 +119,82 @@ __device__ void upper_inverse_smem(const float* R, float* X, int n) {
 // Cholesky G = R^T R (G FP64 in global, computed in FP32 in shared memory),
 // then Rinv = R^{-1} and Racc <- R Racc (or Racc = R when init).
 // Shared memory: 3 n x n FP32 matrices (n <= 128 -> 192 KB).
+//
+// mode: CHOL_PLAIN       plain Cholesky (a non-positive pivot is a breakdown);
+//       CHOL_SHIFT_IF_NEEDED  plain first; on breakdown retry with the shift of
+//                         shifted CholeskyQR (Fukaya et al. 2020) and set
+//                         *needs_more = 1 so the caller's optional pass runs;
+//       CHOL_IF_FLAGGED  run only when *needs_more != 0 (else write nothing).
+// The elimination keeps unscaled Schur complements (A(i,c) -= A(i,j) A(c,j) /
+// d_j with pivot d_j), so each column costs one barrier; L(i,j) =
+// A(i,j) / sqrt(d_j) is formed at the end.
+__device__ bool chol_smem(float* A, int n, float shift, int tid, int nt) {
+  for (int idx = tid; idx < n; idx += nt) A[idx + idx * n] += shift;
+  __syncthreads();
+  const int tx = tid & 31, ty = tid >> 5;
+  for (int j = 0; j < n; ++j) {
+    const float d = A[j + j * n];
+    if (!(d > 0.f) || !isfinite(d)) return false;  // same decision in every thread
+    const float inv = 1.f / d;
+    for (int c = j + 1 + ty; c < n; c += 32) {
+      const float acj = A[c + j * n] * inv;
+      for (int i = c + tx; i < n; i += 32) A[i + c * n] -= A[i + j * n] * acj;
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int r = idx % n, c = idx / n;
+    if (r > c) A[idx] /= sqrtf(A[c + c * n]);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n; idx += nt) A[idx + idx * n] = sqrtf(A[idx + idx * n]);
+  __syncthreads();
+  return true;
+}
+
 __global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ G, int n, float* Rinv, int ldr,
-                                                        double* Racc, int ldacc, int init_acc, int shifted,
-                                                        int* status) {
+                                                        double* Racc, int ldacc, int init_acc, int mode,
+                                                        int* needs_more, int* status) {
   extern __shared__ float sm[];
   float* L = sm;            // lower Cholesky factor L = R^T, col-major n x n
   float* X = sm + n * n;    // R^{-1}
   float* T = X + n * n;     // scratch (R as upper, col-major)
-  __shared__ int bad;
-  __shared__ float shift;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    bad = 0;
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += G[i + i * n];
-    // Shifted CholeskyQR (Fukaya et al. 2020): G + s I with s a small
-    // multiple of |G| (trace as the estimate), above the FP32 Gram and
-    // Cholesky rounding level, so the factorisation cannot break down; the
-    // following unshifted passes restore orthogonality.
-    shift = shifted ? float(1e-5 * tr) : 0.f;
-  }
+  if (mode == CHOL_IF_FLAGGED && (needs_more == nullptr || *needs_more == 0)) return;
+  __shared__ int nonfinite;
+  if (tid == 0) nonfinite = 0;
   __syncthreads();
+  double tr_part = 0.0;
   for (int idx = tid; idx < n * n; idx += nt) {
     const int r = idx % n, c = idx / n;
     const double g = G[idx];
-    if (!isfinite(g)) bad = LR_ERR_NONFINITE;
-    L[idx] = (r >= c) ? float(g) + (r == c ? shift : 0.f) : 0.f;
+    if (!isfinite(g)) nonfinite = 1;
+    L[idx] = (r >= c) ? float(g) : 0.f;
+    if (r == c) tr_part += g;
   }
   __syncthreads();
-  for (int j = 0; j < n && !bad; ++j) {
-    if (tid == 0) {
-      const float d = L[j + j * n];
-      if (!(d > 0.f) || !isfinite(d)) bad = LR_ERR_BREAKDOWN;
-      else L[j + j * n] = sqrtf(d);
-    }
-    __syncthreads();
-    if (bad) break;
-    const float ljj = L[j + j * n];
-    for (int i = j + 1 + tid; i < n; i += nt) L[i + j * n] /= ljj;
-    __syncthreads();
-    // trailing update of the lower triangle, L(i,c) -= L(i,j) L(c,j) for
-    // j < c <= i; 32 x 32 thread grid: ty walks columns, tx walks rows
-    {
-      const int tx = tid & 31, ty = tid >> 5;
-      for (int c = j + 1 + ty; c < n; c += 32) {
-        const float lcj = L[c + j * n];
-        for (int i = c + tx; i < n; i += 32) L[i + c * n] -= L[i + j * n] * lcj;
-      }
-    }
-    __syncthreads();
+  if (nonfinite) {
+    if (tid == 0) set_status(status, LR_ERR_NONFINITE);
+    return;
   }
-  if (bad) {
-    if (tid == 0) set_status(status, bad);
+  bool ok = chol_smem(L, n, 0.f, tid, nt);
+  if (!ok && mode == CHOL_SHIFT_IF_NEEDED) {
+    // trace(G) as the norm estimate; the shift sits above the FP32 Gram and
+    // Cholesky rounding level, so the factorisation cannot break down.
+    __shared__ double tr;
+    if (tid == 0) tr = 0.0;
+    __syncthreads();
+    atomicAdd(&tr, tr_part);
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int r = idx % n, c = idx / n;
+      L[idx] = (r >= c) ? float(G[idx]) : 0.f;
+    }
+    __syncthreads();
+    ok = chol_smem(L, n, float(1e-5 * tr), tid, nt);
+    if (ok && tid == 0 && needs_more) *needs_more = 1;
+  }
+  if (!ok) {
+    if (tid == 0) set_status(status, LR_ERR_BREAKDOWN);
     // leave a harmless identity so later kernels stay finite
     for (int idx = tid; idx < n * n; idx += nt) {
       const int r = idx % n, c = idx / n;
@@ -443,6 +468,19 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(const float* __restrict__ 
   }
 }
 
+// M (n x n FP32) <- copyltu(M - C) with C FP64 (may be null):
+// out(i,j) = in(max(i,j), min(i,j)), the symmetric matrix built from the
+// lower triangle (used by the thin-QR reverse rule).
+__global__ void qr_bwd_sym_kernel(const float* M, const double* C, int n, float* out) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int i = idx % n, j = idx / n;
+    const int r = max(i, j), c = min(i, j);
+    float v = M[r + c * n];
+    if (C) v -= float(C[r + c * n]);
+    out[idx] = v;
+  }
+}
+
 inline int grid_for(int64_t total) { return int(std::min<int64_t>(4096, std::max<int64_t>(1, (total + 255) / 256))); }
 
 }  // namespace
@@ -467,9 +505,10 @@ void f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, __nv_bfloat1
   LR_LAUNCH_CHECK();
 }
 
-void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s) {
+void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
+              const int* run_if) {
   if (rows <= 0 || cols <= 0) return;
-  copy_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols);
+  copy_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols, run_if);
   LR_LAUNCH_CHECK();
 }
 
@@ -479,8 +518,8 @@ void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t 
   LR_LAUNCH_CHECK();
 }
 
-void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int shifted,
-              int* status, cudaStream_t s) {
+void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int mode,
+              int* needs_more, int* status, cudaStream_t s) {
   LR_REQUIRE(ell >= 1 && ell <= 128, LR_ERR_UNSUPPORTED, "chol_inv: block width must be <= 128");
   const size_t smem = size_t(3) * ell * ell * sizeof(float);
   static bool attr[64] = {};
@@ -490,7 +529,7 @@ void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int 
     LR_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 128 * 128 * 4));
     attr[dev & 63] = true;
   }
-  chol_inv_kernel<<<1, 1024, smem, s>>>(G, ell, Rinv, ldr, Racc, ldacc, init_acc ? 1 : 0, shifted, status);
+  chol_inv_kernel<<<1, 1024, smem, s>>>(G, ell, Rinv, ldr, Racc, ldacc, init_acc ? 1 : 0, mode, needs_more, status);
   LR_LAUNCH_CHECK();
 }
 
@@ -521,6 +560,11 @@ void f64_to_f32(const double* src, int lds, float* dst, int ldd, int rows, int c
 
 void r_to_f32(const double* R, int ldr, int n, float* out, int ldo, bool trans, cudaStream_t s) {
   r_to_f32_kernel<<<grid_for(int64_t(n) * n), 256, 0, s>>>(R, ldr, n, out, ldo, trans ? 1 : 0);
+  LR_LAUNCH_CHECK();
+}
+
+void qr_bwd_sym(const float* M, const double* C, int n, float* out, cudaStream_t s) {
+  qr_bwd_sym_kernel<<<grid_for(int64_t(n) * n), 256, 0, s>>>(M, C, n, out);
   LR_LAUNCH_CHECK();
 }
 
