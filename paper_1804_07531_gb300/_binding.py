@@ -164,10 +164,10 @@ class Handle:
             msg = lib().lr_last_error(self.h).decode()
             raise LowrankError(st, msg)
 
-    def reserve(self, m, n, ell1, ell2=0, v=2):
+    def reserve(self, m, n, ell1, ell2=0, v=2, extra=0):
         size = ctypes.c_size_t()
         self.check(lib().lr_workspace_size(self.h, m, n, ell1, ell2, v, ctypes.byref(size)))
-        need = size.value
+        need = size.value + int(extra)
         if self.ws is None or self.ws.numel() < need:
             self.ws = torch.empty(need + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
             ptr = (self.ws.data_ptr() + 255) // 256 * 256

@@ -9,6 +9,7 @@
 // (thin QR by block CholeskyQR2).  Every step runs in this library's kernels.
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -33,6 +34,10 @@ struct lr_handle_s {
   std::vector<lr_trace_rec> recs;
   double acc_ms[LR_TRACE_COUNT] = {};
   int64_t acc_n[LR_TRACE_COUNT] = {};
+  // host-streamed sketches: a copy stream and per-buffer events (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  cudaEvent_t consumed[2] = {nullptr, nullptr};
 };
 
 namespace lr {
@@ -321,6 +326,40 @@ void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
   }
 }
 
+// ------------------------------------------------ triangular inverse
+// X = R^{-1} (FP32 n x n, ld n) for an upper-triangular FP64 R (ld n) of any
+// width: diagonal blocks of <= 128 are inverted in one CTA each, the blocks
+// above the diagonal follow from X_IJ = -X_II (sum_{K=I+1..J} R_IK X_KJ),
+// computed block column by block column, bottom up, as small GEMMs.
+void tri_inv_any(Ctx& c, const double* R, int n, float* X) {
+  ArenaScope sc(c.ar);
+  const int nb = (n + kMaxBlock - 1) / kMaxBlock;
+  const int b = (n + nb - 1) / nb;
+  float* R32 = c.ar.take<float>(size_t(n) * n);
+  float* T = c.ar.take<float>(size_t(b) * b);
+  if (c.measure) return;
+  if (nb == 1) {
+    tri_inv(R, n, n, X, n, c.status, c.s);
+    return;
+  }
+  auto start = [&](int I) { return I * b; };
+  auto size = [&](int I) { return std::min(b, n - I * b); };
+  r_to_f32(R, n, n, R32, n, false, c.s);
+  LR_CHECK_CUDA(cudaMemsetAsync(X, 0, sizeof(float) * size_t(n) * n, c.s));
+  for (int J = 0; J < nb; ++J)
+    tri_inv(R + start(J) + int64_t(start(J)) * n, n, size(J), X + start(J) + int64_t(start(J)) * n, n, c.status, c.s);
+  for (int J = 1; J < nb; ++J)
+    for (int I = J - 1; I >= 0; --I) {
+      const int k0 = start(I + 1), kl = start(J) + size(J) - k0;
+      // T = R[I, I+1..J] X[I+1..J, J]
+      gemm(c, size(I), size(J), kl, false, R32 + start(I) + int64_t(k0) * n, n, false,
+           X + k0 + int64_t(start(J)) * n, n, T, size(I));
+      // X_IJ = -X_II T
+      gemm(c, size(I), size(J), size(I), false, X + start(I) + int64_t(start(I)) * n, n, false, T, size(I),
+           X + start(I) + int64_t(start(J)) * n, n, -1.f, 0.f);
+    }
+}
+
 // --------------------------------------------------------- core SVD
 // R (n x n upper, FP64) = Left diag(S) Right^T, outputs FP32 n x n.
 // One-sided Jacobi runs on R^T: the rows of R are graded for the bases
@@ -424,7 +463,6 @@ void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Out
 
 // ------------------------------------------------------- Section 7.3
 void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o) {
-  LR_REQUIRE(ell <= kMaxBlock, LR_ERR_UNSUPPORTED, "row-streamed block Krylov needs ell <= 128");
   ArenaScope sc(c.ar);
   const int Lk = (v - 1) * ell;
   Mat K{c.ar.take<float>(size_t(A.n) * Lk), A.n, Lk, A.n};
@@ -442,8 +480,8 @@ void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat&
     view_chained(c, A, x, Y, Z);         // Y = A X, Z = A^T Y from one read
     orth(c, Y, Rc);                      // Y = Q_c R_c
     Mat blk{K.col(int64_t(i - 1) * ell), A.n, ell, A.n};
+    tri_inv_any(c, Rc, ell, Ri);
     if (!c.measure) {
-      tri_inv(Rc, ell, ell, Ri, ell, c.status, c.s);
       gemm(c, A.n, ell, ell, false, Z.p, Z.ld, false, Ri, ell, blk.p, blk.ld);  // A^T Q_c = Z R_c^{-1}
     }
     if (i < v - 1) orth(c, blk, nullptr, true);
@@ -458,7 +496,6 @@ void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat&
 
 // ------------------------------------------------------- Section 6.7
 void run_rowwise_qb(Ctx& c, const AMat& A, int k, int ell, const Mat& Om, Outs& o) {
-  LR_REQUIRE(ell <= kMaxBlock, LR_ERR_UNSUPPORTED, "row-streamed single pass needs ell <= 128");
   ArenaScope sc(c.ar);
   Mat Y{c.ar.take<float>(size_t(A.m) * ell), A.m, ell, A.m};
   Mat Z{c.ar.take<float>(size_t(A.n) * ell), A.n, ell, A.n};
@@ -471,23 +508,26 @@ void run_rowwise_qb(Ctx& c, const AMat& A, int k, int ell, const Mat& Om, Outs& 
   float* Sv = c.ar.take<float>(size_t(ell));
   view_chained(c, A, Om, Y, Z);          // Y_c = A Omega, Y^_r = A^T Y_c
   orth(c, Y, Rc);                        // [Q_c, R_c] = qr(Y_c)
-  if (!c.measure) {
-    tri_inv(Rc, ell, ell, Ri, ell, c.status, c.s);
-    gemm(c, A.n, ell, ell, false, Z.p, Z.ld, false, Ri, ell, Bt.p, Bt.ld);  // B^T = Y^_r R_c^{-1}
-  }
+  tri_inv_any(c, Rc, ell, Ri);
+  gemm(c, A.n, ell, ell, false, Z.p, Z.ld, false, Ri, ell, Bt.p, Bt.ld);  // B^T = Y^_r R_c^{-1}
   orth(c, Bt, Rb);                       // B^T = Q_b R_b
   core_svd(c, Rb, ell, W, Vj, Sv);       // R_b = V^ L U^T
   write_outputs(c, Y, Vj, Bt, W, ell, Sv, k, o);
 }
 
 // ------------------------------------------------------------ Alg. 7
-void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const Mat& Psi, Outs& o) {
+// `sketch` fills Y (m x ell1) = A Omega and Z (n x ell2) = A^T Psi; by
+// default from one read of a device-resident A (view_dual), for the
+// host-streamed form from column panels copied in from pinned host memory.
+using Sketcher = std::function<void(Ctx&, Mat, Mat)>;
+
+void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const Mat& Psi, Outs& o,
+                     const Sketcher& sketch = nullptr) {
   ArenaScope sc(c.ar);
   const int ell1 = int(Om.cols), ell2 = int(Psi.cols);
   const int l1 = ell1 - k;
   const int lc = (l_c < 0 || l_c > l1) ? l1 : l_c;
   const int Lc = k + lc;
-  LR_REQUIRE(Lc <= kMaxBlock, LR_ERR_UNSUPPORTED, "single pass needs k + l_c <= 128");
   Mat Y{c.ar.take<float>(size_t(A.m) * ell1), A.m, ell1, A.m};
   Mat Z{c.ar.take<float>(size_t(A.n) * ell2), A.n, ell2, A.n};
   double* Rc = c.ar.take<double>(size_t(ell1) * ell1);
@@ -506,7 +546,8 @@ void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const
   float* Vj = c.ar.take<float>(size_t(Lc) * Lc);
   float* Sv = c.ar.take<float>(size_t(Lc));
 
-  view_dual(c, A, Om, Y, Psi, Z);        // a) Y_c = A Omega_r, b) Y_r = A^T Omega_c
+  if (sketch) sketch(c, Y, Z);            // a) Y_c = A Omega_r, b) Y_r = A^T Omega_c
+  else view_dual(c, A, Om, Y, Psi, Z);
   orth(c, Y, Rc);                        // [Q_c, R_c] = qr(Y_c)
   Mat Qc = Y;
   if (lc < l1) {
@@ -518,7 +559,7 @@ void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const
   if (!c.measure) f64_to_f32(P64, ell2, P.p, P.ld, ell2, Lc, c.s);
   orth(c, P, Rh);                        // [Q^, R^] = qr(Omega_c^T Q_c)
   gemm(c, A.n, Lc, ell2, false, Z.p, Z.ld, false, P.p, P.ld, Wz.p, Wz.ld);  // Y_r Q^
-  if (!c.measure) tri_inv(Rh, Lc, Lc, Rhi, Lc, c.status, c.s);
+  tri_inv_any(c, Rh, Lc, Rhi);
   gemm(c, A.n, Lc, Lc, false, Wz.p, Wz.ld, true, Rhi, Lc, Xt.p, Xt.ld);    // X^T = Y_r Q^ R^{-T}
   orth(c, Xt, Rx);                       // X^T = Q_x R_x
   core_svd(c, Rx, Lc, W, Vj, Sv);        // R_x = W S Vj^T, X = Vj S (Q_x W)^T
@@ -602,7 +643,7 @@ void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const M
     if (have_qb) copy_f32(Qb, rows, rhs, rows, rows, ell, c.s);
     gemm(c, rows, ell, ell, false, Q.p, Q.ld, false, Ms, ell, rhs, rows, 1.f, have_qb ? 1.f : 0.f);
     // Bb = rhs R^{-T}, written into this view's panel slot
-    tri_inv(R, ell, ell, Ri, ell, c.status, c.s);
+    tri_inv_any(c, R, ell, Ri);
     Mat Bb = odd ? lslot(j) : rslot(j);
     gemm(c, rows, ell, ell, false, rhs, rows, true, Ri, ell, Bb.p, Bb.ld);
     if (j > 1) {
@@ -615,6 +656,62 @@ void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const M
   }
   // ---- dA = Lc Rc^T, one GEMM (as column-major: dA^T = Rc Lc^T)
   gemm(c, n, m, int64_t(v) * ell, false, Rc.p, Rc.ld, true, Lc.p, Lc.ld, dA, ldda);
+}
+
+// ------------------------------------------------- host streaming
+// The streaming model of Section 6.1 (A = sum_i H_i, each update seen once)
+// with H_i = the i-th column panel of a pinned host A: panel i is copied to
+// one of two device panel buffers on the handle's copy stream while the
+// previous panel is sketched on the caller's stream; for every panel,
+//   Y += A_P Omega[P, :]   and   Z[P, :] = A_P^T Psi,
+// so A crosses the host link exactly once.  Events order each buffer's
+// reuse after its sketches and each sketch after its copy.
+struct HostA {
+  const float* p = nullptr;
+  int64_t m = 0, n = 0, ld = 0;
+};
+
+void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const Mat& Psi, Mat Y, Mat Z) {
+  ArenaScope sc(c.ar);
+  float* buf[2];
+  buf[0] = c.ar.take<float>(size_t(H.m) * pc);
+  buf[1] = c.ar.take<float>(size_t(H.m) * pc);
+  if (c.measure) return;
+  lr_handle h = c.h;
+  if (!h->copy_stream) {
+    LR_CHECK_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      LR_CHECK_CUDA(cudaEventCreateWithFlags(&h->copied[i], cudaEventDisableTiming));
+      LR_CHECK_CUDA(cudaEventCreateWithFlags(&h->consumed[i], cudaEventDisableTiming));
+    }
+  }
+  zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
+  zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
+  // the copy stream starts after everything already queued on the caller's stream
+  LR_CHECK_CUDA(cudaEventRecord(h->consumed[0], c.s));
+  LR_CHECK_CUDA(cudaStreamWaitEvent(h->copy_stream, h->consumed[0], 0));
+  LR_CHECK_CUDA(cudaEventRecord(h->consumed[1], c.s));
+  const int npan = int((H.n + pc - 1) / pc);
+  for (int i = 0; i < npan; ++i) {
+    const int b = i & 1;
+    const int64_t c0 = int64_t(i) * pc, w = std::min(pc, H.n - c0);
+    LR_CHECK_CUDA(cudaStreamWaitEvent(h->copy_stream, h->consumed[b], 0));
+    LR_CHECK_CUDA(cudaMemcpy2DAsync(buf[b], size_t(w) * sizeof(float), H.p + c0, size_t(H.ld) * sizeof(float),
+                                    size_t(w) * sizeof(float), size_t(H.m), cudaMemcpyHostToDevice, h->copy_stream));
+    LR_CHECK_CUDA(cudaEventRecord(h->copied[b], h->copy_stream));
+    LR_CHECK_CUDA(cudaStreamWaitEvent(c.s, h->copied[b], 0));
+    AMat P;
+    P.p = buf[b];
+    P.m = H.m;
+    P.n = w;
+    P.ld = w;
+    P.bf16 = false;
+    // Y += A_P Omega[c0 : c0 + w, :]
+    view_band(c, P, 0, Om.p + c0, Om.ld, int(Om.cols), Y.p, Y.ld, 0, H.m);
+    // Z[c0 : c0 + w, :] = A_P^T Psi
+    view_band(c, P, 1, Psi.p, Psi.ld, int(Psi.cols), Z.p + c0, Z.ld, 0, H.m);
+    LR_CHECK_CUDA(cudaEventRecord(h->consumed[b], c.s));
+  }
 }
 
 // ------------------------------------------------------- validation
@@ -721,6 +818,11 @@ lr_status lr_destroy(lr_handle h) {
   cudaSetDevice(h->device);
   cudaFree(h->status_dev);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  for (int i = 0; i < 2; ++i) {
+    if (h->copied[i]) cudaEventDestroy(h->copied[i]);
+    if (h->consumed[i]) cudaEventDestroy(h->consumed[i]);
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
   return LR_OK;
 }
@@ -795,12 +897,9 @@ lr_status lr_workspace_size(lr_handle h, int64_t m, int64_t n, int ell1, int ell
       const int k = 1;
       measure([&](Ctx& c) { run_subspace(c, A, k, ell1, vv, Om, o); });
       measure([&](Ctx& c) { run_krylov(c, A, k, ell1, vv, Om, o); });
-      if (ell1 <= kMaxBlock) {
-        measure([&](Ctx& c) { run_krylov_rowwise(c, A, k, ell1, vv, Om, o); });
-        measure([&](Ctx& c) { run_rowwise_qb(c, A, k, ell1, Om, o); });
-      }
-      if (!A.bf16 && ell1 <= kMaxBlock)
-        measure([&](Ctx& c) { run_subspace_backward(c, A, 1, ell1, vv, Om, nullptr, nullptr, 0); });
+      measure([&](Ctx& c) { run_krylov_rowwise(c, A, k, ell1, vv, Om, o); });
+      measure([&](Ctx& c) { run_rowwise_qb(c, A, k, ell1, Om, o); });
+      if (!A.bf16) measure([&](Ctx& c) { run_subspace_backward(c, A, 1, ell1, vv, Om, nullptr, nullptr, 0); });
       if (ell2 >= ell1) {
         Mat Ps{nullptr, m, ell2, m};
         measure([&](Ctx& c) { run_single_pass(c, A, std::max(1, ell1 - 1), -1, Om, Ps, o); });
@@ -930,9 +1029,33 @@ lr_status lr_single_pass(lr_handle h, const lr_mat* A, int k, const lr_mat* Omeg
   });
 }
 
-lr_status lr_single_pass_host(lr_handle h, const lr_mat*, int64_t, int, const lr_mat*, const lr_mat*, lr_mat*,
-                              lr_mat*, lr_mat*, const lr_opts*, void*) {
-  return guarded(h, [&] { throw Error{LR_ERR_UNSUPPORTED, "host-streamed single pass is not built yet"}; });
+lr_status lr_single_pass_host(lr_handle h, const lr_mat* A_host, int64_t panel_cols, int k, const lr_mat* Omega,
+                              const lr_mat* Psi, lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    LR_REQUIRE(A_host && A_host->data, LR_ERR_INVALID_ARG, "A_host is NULL");
+    LR_REQUIRE(A_host->dtype == LR_F32 && A_host->col_major == 0, LR_ERR_DTYPE, "A_host must be F32 row-major");
+    LR_REQUIRE(A_host->rows >= 1 && A_host->cols >= 1 && A_host->ld >= A_host->cols, LR_ERR_SHAPE, "bad A_host");
+    LR_REQUIRE(panel_cols >= 1, LR_ERR_INVALID_ARG, "panel_cols must be positive");
+    cudaPointerAttributes pa{};
+    LR_CHECK_CUDA(cudaPointerGetAttributes(&pa, A_host->data));
+    LR_REQUIRE(pa.type == cudaMemoryTypeHost, LR_ERR_INVALID_ARG, "A_host must be pinned (page-locked) host memory");
+    AMat a;  // shapes only; the data stays on the host
+    a.m = A_host->rows;
+    a.n = A_host->cols;
+    a.ld = A_host->ld;
+    a.bf16 = false;
+    LR_REQUIRE(Omega && Psi, LR_ERR_INVALID_ARG, "Omega and Psi are required");
+    Mat om = check_thin(Omega, a.n, -1, "Omega");
+    Mat ps = check_thin(Psi, a.m, -1, "Psi");
+    LR_REQUIRE(k >= 1 && om.cols > k && ps.cols >= om.cols && ps.cols <= std::min(a.m, a.n), LR_ERR_INVALID_ARG,
+               "need ell2 >= ell1 > k and ell2 <= min(m, n)");
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    HostA H{static_cast<const float*>(A_host->data), a.m, a.n, A_host->ld};
+    const int64_t pc = std::min<int64_t>(panel_cols, a.n);
+    run_single_pass(c, a, k, opts ? opts->l_c : -1, om, ps, o,
+                    [&](Ctx& cc, Mat Y, Mat Z) { sketch_host_panels(cc, H, pc, om, ps, Y, Z); });
+  });
 }
 
 lr_status lr_subspace_iter_backward(lr_handle h, const lr_mat* A, int k, int p, int v, const lr_mat* Omega,
@@ -941,7 +1064,6 @@ lr_status lr_subspace_iter_backward(lr_handle h, const lr_mat* A, int k, int p, 
     AMat a = check_A(A);
     LR_REQUIRE(!a.bf16, LR_ERR_DTYPE, "the reverse pass needs an F32 A");
     check_kpv(a, k, p, v, 2);
-    LR_REQUIRE(k + p <= kMaxBlock, LR_ERR_UNSUPPORTED, "the reverse pass needs k + p <= 128");
     Mat om = check_thin(Omega, a.n, k + p, "Omega");
     LR_REQUIRE(dS && dS->data && dS->dtype == LR_F32 && dS->rows * dS->cols >= k, LR_ERR_SHAPE,
                "dS must hold k F32 weights");

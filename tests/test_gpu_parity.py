@@ -242,3 +242,21 @@ def test_wide_core_svd_parity(algo, m, n, k, p, v):
     assert_status_ok()
     uo, so, vo = ref(a64, om.astype(np.float64), k, v)
     print(check_tsvd(a64, u, s, vv, uo, so, vo))
+
+
+@pytest.mark.parametrize("panel", [512, 1000, 4096])
+def test_host_streamed_single_pass_matches_device_and_oracle(panel):
+    """Column panels of a pinned host A (ragged last panel) give the same
+    factorisation as the device-resident single pass and the oracle."""
+    m, n, k, ell1, ell2 = 4096, 3000, 20, 40, 80
+    a64 = S.usv(m, n, S.sigma_config("inv", n), 81, 82) + 1e-5 * S.gaussian(m, n, seed=83)
+    a32 = a64.astype(np.float32)
+    om = S.gaussian(n, ell1, seed=84).astype(np.float32)
+    ps = S.gaussian(m, ell2, seed=85).astype(np.float32)
+    ah = torch.tensor(a32).pin_memory()
+    u, s, vv = api().single_pass_host(ah, k, torch.tensor(om), torch.tensor(ps), panel_cols=panel)
+    assert_status_ok()
+    ud, sd, vd = api().single_pass(t32(a32), k, t32(om), t32(ps))
+    assert np.abs(f64(s) - f64(sd)).max() / f64(sd)[0] < 1e-6
+    uo, so, vo = Al.single_pass(a32.astype(np.float64), om.astype(np.float64), ps.astype(np.float64), k)
+    print(check_tsvd(a32.astype(np.float64), u, s, vv, uo, so, vo))
