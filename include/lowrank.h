@@ -75,8 +75,11 @@ typedef struct {
   int32_t l_c;              /* Alg. 7 truncation oversampling; < 0 means l_c = l_1 */
   int32_t enhanced;         /* lr_block_krylov: 1 = row-streamed variant of Section 7.3 */
   int32_t split_last;       /* BF16 form: last view's operand as BF16 hi + lo (two products) */
-  int32_t shifted_fallback; /* 1 = on Cholesky breakdown retry with a shifted Gram */
-  int32_t reserved[4];
+  int32_t shifted_fallback; /* kept for compatibility: every thin QR already retries a
+                               breakdown with a shifted Gram (shifted CholeskyQR3) */
+  int32_t band_mb;          /* one-read sketches (dual, chained): MiB of A per L2 band;
+                               0 = default; a value >= the size of A means two full passes */
+  int32_t reserved[3];
 } lr_opts;
 
 typedef struct lr_handle_s* lr_handle;

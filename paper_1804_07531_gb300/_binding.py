@@ -43,7 +43,8 @@ class LrMat(ctypes.Structure):
 
 class LrOpts(ctypes.Structure):
     _fields_ = [("l_c", ctypes.c_int32), ("enhanced", ctypes.c_int32), ("split_last", ctypes.c_int32),
-                ("shifted_fallback", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("shifted_fallback", ctypes.c_int32), ("band_mb", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class LowrankError(RuntimeError):
@@ -199,8 +200,9 @@ def _stream(stream=None) -> int:
     return stream.cuda_stream
 
 
-def _opts(l_c=-1, enhanced=False, split_last=False, shifted_fallback=False) -> LrOpts:
+def _opts(l_c=-1, enhanced=False, split_last=False, shifted_fallback=False, band_mb=0) -> LrOpts:
     o = LrOpts()
+    o.band_mb = int(band_mb)
     o.l_c = -1 if l_c is None else int(l_c)
     o.enhanced = int(bool(enhanced))
     o.split_last = int(bool(split_last))

@@ -37,7 +37,7 @@ def _p(m: LrMat):
     return ctypes.byref(m)
 
 
-def sketch(a, x=None, w=None, stream=None):
+def sketch(a, x=None, w=None, stream=None, band_mb=0):
     """Y = A X and/or Z = A^T W (both from one read of A when both are given)."""
     a, (x, w) = _prep(a, x, w)
     h = Handle.get(a.device)
@@ -55,12 +55,12 @@ def sketch(a, x=None, w=None, stream=None):
             mt = mat_thin(t)
             keep.append(mt)
             args.append(_p(mt))
-    o = _opts()
+    o = _opts(band_mb=band_mb)
     _call(h, lib().lr_sketch, *args, ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return y, z
 
 
-def sketch_chained(a, x, stream=None):
+def sketch_chained(a, x, stream=None, band_mb=0):
     """Y = A X and Z = A^T Y from one read of A (Section 6.7)."""
     a, (x,) = _prep(a, x)
     h = Handle.get(a.device)
@@ -69,7 +69,7 @@ def sketch_chained(a, x, stream=None):
     z = empty_cm(n, x.shape[1], a.device)
     h.reserve(m, n, x.shape[1])
     mA, mx, my, mz = mat_a(a), mat_thin(x), mat_thin(y), mat_thin(z)
-    o = _opts()
+    o = _opts(band_mb=band_mb)
     _call(h, lib().lr_sketch_chained, _p(mA), _p(mx), _p(my), _p(mz), ctypes.byref(o),
           ctypes.c_void_p(_stream(stream)))
     return y, z

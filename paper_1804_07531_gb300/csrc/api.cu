@@ -191,10 +191,15 @@ void view_band(Ctx& c, const AMat& A, int mode, const float* B, int64_t ldb, int
   }
 }
 
-int64_t band_rows(const AMat& A) {
-  // about 48 MB of A per band so a band read by the range product is still
-  // in L2 (129 MB) when the co-range product reads it
-  int64_t r = int64_t(48) * 1024 * 1024 / (A.n * int64_t(A.elem()));
+int64_t band_rows(const AMat& A, int band_mb) {
+  // band_mb > 0: bands of that many MiB of A, each read by the range and the
+  // co-range products back to back so the second read hits L2 (129 MB).
+  // Default (0): one band, i.e. two full passes over A.  Measured on GB300
+  // for a 2 GiB A: two full passes (each near the HBM roof) beat every band
+  // size, because each band costs two launches and partial-tile atomics
+  // that outweigh the HBM bytes saved.
+  if (band_mb <= 0) return A.m;
+  int64_t r = int64_t(band_mb) * 1024 * 1024 / (A.n * int64_t(A.elem()));
   r = std::max<int64_t>(256, r / 256 * 256);
   return std::min<int64_t>(r, (A.m + 255) / 256 * 256);
 }
@@ -230,7 +235,7 @@ void view_dual(Ctx& c, const AMat& A, const Mat& X, Mat Y, const Mat& W, Mat Z) 
   if (c.measure) return;
   zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
   zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
-  const int64_t rb = band_rows(A);
+  const int64_t rb = band_rows(A, c.opt.band_mb);
   for (int64_t r0 = 0; r0 < A.m; r0 += rb) {
     const int64_t rows = std::min(rb, A.m - r0);
     view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, xb, ldx);
@@ -256,7 +261,7 @@ void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
   if (c.measure) return;
   zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
   zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
-  const int64_t rb = band_rows(A);
+  const int64_t rb = band_rows(A, c.opt.band_mb);
   for (int64_t r0 = 0; r0 < A.m; r0 += rb) {
     const int64_t rows = std::min(rb, A.m - r0);
     view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, xb, ldx);
