@@ -105,7 +105,7 @@ lr_status lr_set_workspace(lr_handle handle, void* dev_ptr, size_t bytes);
  * *device_status and clear it. */
 lr_status lr_get_status(lr_handle handle, void* stream, int* device_status);
 
-/* One view of A (Section 4, Alg. 2 lines 4 and 6; Section 6.4, Alg. 7 line 3):
+/* One view of A (Section 4 and Alg. 2; the sketches of Section 6.4, Alg. 7):
  *   Y = A X   (X: n x ell1, Y: m x ell1) when X != NULL,
  *   Z = A^T W (W: m x ell2, Z: n x ell2) when W != NULL.
  * With both X and W the two products share one read of A from HBM (the

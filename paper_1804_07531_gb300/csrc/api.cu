@@ -132,62 +132,96 @@ void gram64(Ctx& c, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
 // out (rows_out x ell) = A[r0:r0+rows, :] B (mode 0, out = Y rows r0..) or
 // += A[r0:r0+rows, :]^T B[r0:r0+rows, :] (mode 1, out = Z).  The output must
 // be zeroed by the caller before the first contribution.
-void view_band(Ctx& c, const AMat& A, int mode, const float* B, int64_t ldb, int ell, float* out, int64_t ldo,
-               int64_t r0, int64_t rows, const __nv_bfloat16* Bb = nullptr, int64_t ldbb = 0) {
-  if (rows <= 0) return;
+// Pre-converted thin operand (full operand rows; mode 1 offsets by r0):
+// BF16 copy for a BF16 A, TF32 hi/lo split for an F32 A.
+struct SplitOp {
+  const __nv_bfloat16* bf = nullptr;
+  const float* hi = nullptr;
+  const float* lo = nullptr;
+  int64_t ld = 0;
+};
+
+inline int64_t round4(int64_t x) { return (x + 3) / 4 * 4; }
+
+// Converts the thin operand (rows x ell) into the form the view kernel of
+// A's precision reads.
+SplitOp convert_operand(Ctx& c, const AMat& A, const float* B, int64_t ldb, int64_t rows, int ell) {
+  SplitOp o;
   if (A.bf16) {
+    o.ld = round8(rows);
+    auto* t = c.ar.take<__nv_bfloat16>(size_t(o.ld) * ell);
+    if (!c.measure) f32_to_bf16(B, ldb, t, nullptr, o.ld, rows, ell, c.s);
+    o.bf = t;
+  } else {
+    o.ld = round4(rows);
+    float* h = c.ar.take<float>(size_t(o.ld) * ell);
+    float* l = c.ar.take<float>(size_t(o.ld) * ell);
+    if (!c.measure) split_tf32(B, ldb, h, l, o.ld, rows, ell, c.s);
+    o.hi = h;
+    o.lo = l;
+  }
+  return o;
+}
+
+void view_band(Ctx& c, const AMat& A, int mode, const float* B, int64_t ldb, int ell, float* out, int64_t ldo,
+               int64_t r0, int64_t rows, const SplitOp* pre = nullptr) {
+  if (rows <= 0) return;
+  {
     ArenaScope sc(c.ar);
-    const __nv_bfloat16* op = Bb;
-    int64_t ldop = ldbb;
-    const int64_t orows = (mode == 0) ? A.n : rows;
-    if (!op) {
-      ldop = round8(orows);
-      __nv_bfloat16* tmp = c.ar.take<__nv_bfloat16>(size_t(ldop) * ell);
-      if (!c.measure) f32_to_bf16(mode == 0 ? B : B + r0, ldb, tmp, nullptr, ldop, orows, ell, c.s);
-      op = tmp;
-    } else if (mode == 1) {
-      op = Bb + r0;
+    SplitOp op;
+    if (pre) {
+      op = *pre;
+    } else {
+      const int64_t orows = (mode == 0) ? A.n : rows;
+      op = convert_operand(c, A, mode == 0 ? B : B + r0, ldb, orows, ell);
+      if (mode == 1) {  // converted from the band's rows: index from row 0
+        if (op.bf) op.bf -= r0;
+        if (op.hi) {
+          op.hi -= r0;
+          op.lo -= r0;
+        }
+      }
     }
     if (c.measure) return;
     TraceScope tr(c, mode == 0 ? LR_TRACE_VIEW_RANGE : LR_TRACE_VIEW_CORANGE);
     for (int g0 = 0; g0 < ell; g0 += 256) {
       const int w = std::min(256, ell - g0);
-      ViewBf16Args a;
-      a.device = c.h->device;
-      a.mode = mode;
-      a.A = A.b();
-      a.lda = A.ld;
-      a.row0 = r0;
-      a.rows = rows;
-      a.n = A.n;
-      a.B = op + int64_t(g0) * ldop;
-      a.ldb = ldop;
-      a.ell = w;
-      a.out = (mode == 0 ? out + r0 : out) + int64_t(g0) * ldo;
-      a.ldo = ldo;
-      a.status = c.status;
-      view_bf16(a, c.s);
+      if (A.bf16) {
+        ViewBf16Args a;
+        a.device = c.h->device;
+        a.mode = mode;
+        a.A = A.b();
+        a.lda = A.ld;
+        a.row0 = r0;
+        a.rows = rows;
+        a.n = A.n;
+        a.B = op.bf + (mode == 1 ? r0 : 0) + int64_t(g0) * op.ld;
+        a.ldb = op.ld;
+        a.ell = w;
+        a.out = (mode == 0 ? out + r0 : out) + int64_t(g0) * ldo;
+        a.ldo = ldo;
+        a.status = c.status;
+        view_bf16(a, c.s);
+      } else {
+        ViewTf32Args a;
+        a.device = c.h->device;
+        a.mode = mode;
+        a.A = A.f();
+        a.lda = A.ld;
+        a.row0 = r0;
+        a.rows = rows;
+        a.n = A.n;
+        a.Bhi = op.hi + (mode == 1 ? r0 : 0) + int64_t(g0) * op.ld;
+        a.Blo = op.lo + (mode == 1 ? r0 : 0) + int64_t(g0) * op.ld;
+        a.ldb = op.ld;
+        a.ell = w;
+        a.out = (mode == 0 ? out + r0 : out) + int64_t(g0) * ldo;
+        a.ldo = ldo;
+        a.status = c.status;
+        view_tf32x3(a, c.s);
+      }
     }
-  } else {
-    if (c.measure) return;
-    TraceScope tr(c, mode == 0 ? LR_TRACE_VIEW_RANGE : LR_TRACE_VIEW_CORANGE);
-    GemmArgs g;
-    g.mode = GEMM_ATOMIC_F32;
-    g.ldb = ldb;
-    g.ldc = ldo;
-    if (mode == 0) {
-      g.M = rows; g.N = ell; g.K = A.n; g.ta = true;
-      g.A = A.f() + r0 * A.ld; g.lda = A.ld;
-      g.B = B;
-      g.C = out + r0;
-    } else {
-      g.M = A.n; g.N = ell; g.K = rows; g.ta = false;
-      g.A = A.f() + r0 * A.ld; g.lda = A.ld;
-      g.B = B + r0;
-      g.C = out;
-    }
-    g.split_k = split_for(g.M, g.N, g.K, c.sms);
-    sgemm(g, c.s);
+    return;
   }
 }
 
@@ -215,48 +249,36 @@ void view_corange(Ctx& c, const AMat& A, const Mat& W, Mat Z) {
   view_band(c, A, 1, W.p, W.ld, int(W.cols), Z.p, Z.ld, 0, A.m);
 }
 
-// Y = A X and Z = A^T W sharing each L2-sized band of A (Alg. 7 line 3).
+// Y = A X and Z = A^T W (the two sketches of Alg. 7).  The operands are
+// converted once; the bands of band_rows() are swept by the range and then
+// the co-range kernel (by default one band: two full passes over A).
 void view_dual(Ctx& c, const AMat& A, const Mat& X, Mat Y, const Mat& W, Mat Z) {
   ArenaScope sc(c.ar);
-  const __nv_bfloat16 *xb = nullptr, *wb = nullptr;
-  int64_t ldx = 0, ldw = 0;
-  if (A.bf16) {
-    ldx = round8(A.n);
-    ldw = round8(A.m);
-    auto* tx = c.ar.take<__nv_bfloat16>(size_t(ldx) * X.cols);
-    auto* tw = c.ar.take<__nv_bfloat16>(size_t(ldw) * W.cols);
-    if (!c.measure) {
-      f32_to_bf16(X.p, X.ld, tx, nullptr, ldx, A.n, X.cols, c.s);
-      f32_to_bf16(W.p, W.ld, tw, nullptr, ldw, A.m, W.cols, c.s);
-    }
-    xb = tx;
-    wb = tw;
-  }
+  const SplitOp xo = convert_operand(c, A, X.p, X.ld, A.n, int(X.cols));
+  const SplitOp wo = convert_operand(c, A, W.p, W.ld, A.m, int(W.cols));
   if (c.measure) return;
   zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
   zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
   const int64_t rb = band_rows(A, c.opt.band_mb);
   for (int64_t r0 = 0; r0 < A.m; r0 += rb) {
     const int64_t rows = std::min(rb, A.m - r0);
-    view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, xb, ldx);
-    view_band(c, A, 1, W.p, W.ld, int(W.cols), Z.p, Z.ld, r0, rows, wb, ldw);
+    view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, &xo);
+    view_band(c, A, 1, W.p, W.ld, int(W.cols), Z.p, Z.ld, r0, rows, &wo);
   }
 }
 
-// Y = A X and Z = A^T Y, band by band (Section 6.7: each band of rows is used
-// for its slice of Y and, while it is still in L2, for its share of A^T Y).
+// Y = A X and Z = A^T Y (Section 6.7): each band of rows gives its slice of
+// Y, which is converted and used for that band's share of A^T Y.
 void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
   ArenaScope sc(c.ar);
-  const __nv_bfloat16 *xb = nullptr;
-  __nv_bfloat16* yb = nullptr;
-  int64_t ldx = 0, ldyb = 0;
+  const SplitOp xo = convert_operand(c, A, X.p, X.ld, A.n, int(X.cols));
+  SplitOp yo;
+  yo.ld = A.bf16 ? round8(A.m) : round4(A.m);
   if (A.bf16) {
-    ldx = round8(A.n);
-    ldyb = round8(A.m);
-    auto* tx = c.ar.take<__nv_bfloat16>(size_t(ldx) * X.cols);
-    yb = c.ar.take<__nv_bfloat16>(size_t(ldyb) * Y.cols);
-    if (!c.measure) f32_to_bf16(X.p, X.ld, tx, nullptr, ldx, A.n, X.cols, c.s);
-    xb = tx;
+    yo.bf = c.ar.take<__nv_bfloat16>(size_t(yo.ld) * Y.cols);
+  } else {
+    yo.hi = c.ar.take<float>(size_t(yo.ld) * Y.cols);
+    yo.lo = c.ar.take<float>(size_t(yo.ld) * Y.cols);
   }
   if (c.measure) return;
   zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
@@ -264,9 +286,13 @@ void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
   const int64_t rb = band_rows(A, c.opt.band_mb);
   for (int64_t r0 = 0; r0 < A.m; r0 += rb) {
     const int64_t rows = std::min(rb, A.m - r0);
-    view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, xb, ldx);
-    if (A.bf16) f32_to_bf16(Y.p + r0, Y.ld, yb + r0, nullptr, ldyb, rows, Y.cols, c.s);
-    view_band(c, A, 1, Y.p, Y.ld, int(Y.cols), Z.p, Z.ld, r0, rows, yb, ldyb);
+    view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, &xo);
+    if (A.bf16)
+      f32_to_bf16(Y.p + r0, Y.ld, const_cast<__nv_bfloat16*>(yo.bf) + r0, nullptr, yo.ld, rows, Y.cols, c.s);
+    else
+      split_tf32(Y.p + r0, Y.ld, const_cast<float*>(yo.hi) + r0, const_cast<float*>(yo.lo) + r0, yo.ld, rows,
+                 Y.cols, c.s);
+    view_band(c, A, 1, Y.p, Y.ld, int(Y.cols), Z.p, Z.ld, r0, rows, &yo);
   }
 }
 
@@ -404,7 +430,7 @@ void run_subspace(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, O
   float* W = c.ar.take<float>(size_t(ell) * ell);
   float* Vj = c.ar.take<float>(size_t(ell) * ell);
   float* Sv = c.ar.take<float>(size_t(ell));
-  Mat cur = Om;  // Q_r = Omega (Alg. 2 line 1: the raw Gaussian)
+  Mat cur = Om;  // Q_r = Omega (Alg. 2 starts from the raw Gaussian)
   for (int j = 1; j <= v; ++j) {
     if (j % 2 == 1) {
       view_range(c, A, cur, Qc);       // A Q_r
@@ -611,6 +637,8 @@ void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const M
   if (c.measure) {  // account for the helpers' own temporaries
     orth(c, Mat{nullptr, mx, ell, mx}, nullptr);
     core_svd(c, nullptr, ell, nullptr, nullptr, nullptr);
+    view_range(c, A, Mat{nullptr, n, ell, n}, Mat{nullptr, m, ell, m});
+    view_corange(c, A, Mat{nullptr, m, ell, m}, Mat{nullptr, n, ell, n});
     return;
   }
   copy_f32(Om.p, Om.ld, rslot(1).p, n, n, ell, c.s);
@@ -679,9 +707,15 @@ struct HostA {
 void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const Mat& Psi, Mat Y, Mat Z) {
   ArenaScope sc(c.ar);
   float* buf[2];
-  buf[0] = c.ar.take<float>(size_t(H.m) * pc);
-  buf[1] = c.ar.take<float>(size_t(H.m) * pc);
-  if (c.measure) return;
+  const int64_t ldp = round4(pc);  // panel rows padded to a 16-byte stride (TMA)
+  buf[0] = c.ar.take<float>(size_t(H.m) * ldp);
+  buf[1] = c.ar.take<float>(size_t(H.m) * ldp);
+  if (c.measure) {
+    AMat shape;
+    shape.bf16 = false;
+    convert_operand(c, shape, nullptr, 0, H.m, int(Psi.cols));
+    return;
+  }
   lr_handle h = c.h;
   if (!h->copy_stream) {
     LR_CHECK_CUDA(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
@@ -692,6 +726,9 @@ void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const
   }
   zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
   zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
+  AMat shape;  // an F32 A: the co-range operand Psi is split once for all panels
+  shape.bf16 = false;
+  const SplitOp po = convert_operand(c, shape, Psi.p, Psi.ld, H.m, int(Psi.cols));
   // the copy stream starts after everything already queued on the caller's stream
   LR_CHECK_CUDA(cudaEventRecord(h->consumed[0], c.s));
   LR_CHECK_CUDA(cudaStreamWaitEvent(h->copy_stream, h->consumed[0], 0));
@@ -701,7 +738,7 @@ void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const
     const int b = i & 1;
     const int64_t c0 = int64_t(i) * pc, w = std::min(pc, H.n - c0);
     LR_CHECK_CUDA(cudaStreamWaitEvent(h->copy_stream, h->consumed[b], 0));
-    LR_CHECK_CUDA(cudaMemcpy2DAsync(buf[b], size_t(w) * sizeof(float), H.p + c0, size_t(H.ld) * sizeof(float),
+    LR_CHECK_CUDA(cudaMemcpy2DAsync(buf[b], size_t(ldp) * sizeof(float), H.p + c0, size_t(H.ld) * sizeof(float),
                                     size_t(w) * sizeof(float), size_t(H.m), cudaMemcpyHostToDevice, h->copy_stream));
     LR_CHECK_CUDA(cudaEventRecord(h->copied[b], h->copy_stream));
     LR_CHECK_CUDA(cudaStreamWaitEvent(c.s, h->copied[b], 0));
@@ -709,12 +746,12 @@ void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const
     P.p = buf[b];
     P.m = H.m;
     P.n = w;
-    P.ld = w;
+    P.ld = ldp;
     P.bf16 = false;
     // Y += A_P Omega[c0 : c0 + w, :]
     view_band(c, P, 0, Om.p + c0, Om.ld, int(Om.cols), Y.p, Y.ld, 0, H.m);
     // Z[c0 : c0 + w, :] = A_P^T Psi
-    view_band(c, P, 1, Psi.p, Psi.ld, int(Psi.cols), Z.p + c0, Z.ld, 0, H.m);
+    view_band(c, P, 1, Psi.p, Psi.ld, int(Psi.cols), Z.p + c0, Z.ld, 0, H.m, &po);
     LR_CHECK_CUDA(cudaEventRecord(h->consumed[b], c.s));
   }
 }

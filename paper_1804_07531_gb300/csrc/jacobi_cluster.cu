@@ -1,6 +1,6 @@
 // One-sided Jacobi SVD of a square core matrix on a thread-block cluster.
 //
-// The core SVD (tsvd of R_r or R_c, Alg. 2 lines 10/12, Alg. 9 lines 11/16)
+// The core SVD (the final tsvd of R_r or R_c in Alg. 2 and Alg. 9)
 // is an ell x ell problem with ell up to a few hundred.  One SM cannot hold W
 // and V (2 ell^2 FP32 values) for ell > ~160 and its issue rate bounds a
 // sweep at ~0.2 ms for ell = 240; so the rows of W and V are split across

@@ -43,6 +43,26 @@ struct ViewBf16Args {
 void view_bf16(const ViewBf16Args& a, cudaStream_t s);
 int view_bf16_ncol(int ell);
 
+// FP32 form on the tensor cores (3xTF32).  The thin operand is given split:
+// Bhi = x with the low 13 mantissa bits cleared, Blo = x - Bhi (split_tf32);
+// both col-major with the same ld (ld * 4 a multiple of 16 bytes).
+struct ViewTf32Args {
+  int device = 0;
+  int mode = 0;
+  const float* A = nullptr;
+  int64_t lda = 0, row0 = 0, rows = 0, n = 0;
+  const float* Bhi = nullptr;
+  const float* Blo = nullptr;
+  int64_t ldb = 0;
+  int ell = 0;
+  float* out = nullptr;
+  int64_t ldo = 0;
+  int* status = nullptr;
+};
+void view_tf32x3(const ViewTf32Args& a, cudaStream_t s);
+void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd, int64_t rows, int64_t cols,
+                cudaStream_t s);
+
 // ---------------------------------------------------------- elementwise
 void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s);
 void zero_bytes(void* p, size_t bytes, cudaStream_t s);

@@ -1,7 +1,7 @@
 // BF16 views of A on the 5th-generation tensor cores (tcgen05 + TMA).
 //
-// A view multiplies the m x n matrix A by a tall thin matrix (Alg. 2 lines 4
-// and 6, Alg. 7 line 3, Alg. 9 lines 4-5 of Bjarkason 2018):
+// A view multiplies the m x n matrix A by a tall thin matrix (the products
+// with A and A^T in Alg. 2, Alg. 7 and Alg. 9 of Bjarkason 2018):
 //   range view     Y = A X     (mode 0; output rows = rows of A, K = n)
 //   co-range view  Z = A^T W   (mode 1; output rows = cols of A, K = rows)
 // The path is HBM-bound for the widths the method uses (2 ell / sizeof(bf16)
@@ -81,6 +81,13 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_fl
     }
   }
 }
+// mbar_wait for roles in which all 32 lanes wait: a lane that gives up just
+// before the phase completes makes the whole warp give up, so the warp stays
+// converged for the .sync.aligned instructions and __syncwarp that follow.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, status);
+  return __all_sync(0xffffffffu, ok);
+}
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -115,6 +122,18 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t 
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+// kind::tf32: A = B = TF32 (format 2 in bits 7-9, 10-12), D = F32.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n, bool a_mn_major) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t(n) >> 3) << 17) |
+         ((128u >> 4) << 24);
+}
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -286,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     while (it < it_end) {
       const int tile = int(it / kb_n);
       const int64_t seg_end = (it_end < int64_t(tile + 1) * kb_n) ? it_end : int64_t(tile + 1) * kb_n;
-      if (!mbar_wait(acc_full, acc_phase, abort_flag, p.status)) break;
+      if (!mbar_wait_warp(acc_full, acc_phase, abort_flag, p.status)) break;
       tc_fence_after();
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
@@ -316,6 +335,272 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(C::kTmemCols));
+  }
+}
+
+// --------------------------------------------------- FP32 form (3xTF32)
+// FP32 views on the tensor cores with FP32-level accuracy: every operand is
+// split as x = hi + lo with hi = x truncated to TF32 (low 13 mantissa bits
+// cleared) and lo = x - hi (exact in FP32), and the product is
+// hi*hi + hi*lo + lo*hi (the dropped lo*lo and the TF32 rounding of lo are
+// ~2^-21 relative).  A arrives by TMA as raw FP32 and is split in shared
+// memory by four converter warps (hi in place, lo into a twin buffer, then
+// fence.proxy.async so the tensor cores see the generic-proxy writes); the
+// thin operand comes pre-split.  A 128-byte swizzled row holds 32 FP32
+// values, so the descriptors and the 32-byte k-step offsets follow the BF16
+// kernel with K = 8 per tcgen05.mma.  Both operands are K-major: for the
+// co-range view the converter warps also transpose the staged tile (the
+// MN-major operand form the BF16 kernel uses for the co-range view gave
+// wrong products with TF32 operands on this GPU).
+constexpr int kThreadsT = 320;  // TMA, MMA, 4 epilogue, 4 converter warps
+
+template <int MODE, int NCOL, int STAGES>
+struct CfgT {
+  static constexpr uint32_t kABytes = 16384u;            // 128 x 32 FP32
+  static constexpr uint32_t kBBytes = NCOL * 128u;       // NCOL rows x 32 FP32
+  static constexpr uint32_t kStage = 2 * kABytes + 2 * kBBytes;
+  static constexpr uint32_t kTmemCols = NCOL <= 32 ? 32 : NCOL <= 64 ? 64 : NCOL <= 128 ? 128 : 256;
+  static constexpr size_t kSmem = size_t(STAGES) * kStage + 1024 + 256;
+  static_assert(NCOL % 16 == 0 && NCOL >= 16 && NCOL <= 256, "M=128 MMA needs N % 16 == 0, N <= 256");
+};
+
+template <int MODE, int NCOL, int STAGES>
+__global__ void __launch_bounds__(kThreadsT, 1)
+    view_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
+                       const __grid_constant__ CUtensorMap tmBlo, ViewParams p) {
+  using C = CfgT<MODE, NCOL, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * C::kStage);
+  uint64_t* conv = full + STAGES;
+  uint64_t* empty = conv + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t G = gridDim.x;
+  const int64_t it_begin = p.iters_total * blockIdx.x / G;
+  const int64_t it_end = p.iters_total * (blockIdx.x + 1) / G;
+  const int kb_n = p.kblocks;
+  // stage s: [A hi | A lo | B hi | B lo]
+  auto a_hi = [&](int s) { return smem + s * C::kStage; };
+  auto a_lo = [&](int s) { return smem + s * C::kStage + C::kABytes; };
+  auto b_hi = [&](int s) { return smem + s * C::kStage + 2 * C::kABytes; };
+  auto b_lo = [&](int s) { return smem + s * C::kStage + 2 * C::kABytes + C::kBBytes; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 4);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(C::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      uint32_t stage = 0, phase = 0;
+      for (int64_t it = it_begin; it < it_end; ++it) {
+        const int tile = int(it / kb_n);
+        const int kb = int(it % kb_n);
+        if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.status)) break;
+        mbar_expect_tx(&full[stage], C::kABytes + 2 * C::kBBytes);
+        if (MODE == 0) {
+          tma_load_2d(a_hi(stage), &tmA, &full[stage], kb * 32, tile * 128);
+        } else {
+#pragma unroll
+          for (int h = 0; h < 4; ++h) tma_load_2d(a_hi(stage) + h * 4096, &tmA, &full[stage], tile * 128 + h * 32, kb * 32);
+        }
+        tma_load_2d(b_hi(stage), &tmBhi, &full[stage], kb * 32, 0);
+        tma_load_2d(b_lo(stage), &tmBlo, &full[stage], kb * 32, 0);
+        if (++stage == STAGES) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+      if (*abort_flag) {
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 10000000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t kIdesc = idesc_tf32(NCOL, false);  // both operands K-major
+      uint32_t stage = 0, phase = 0, acc_phase = 0;
+      int64_t it = it_begin;
+      bool ok = true;
+      while (ok && it < it_end) {
+        const int tile = int(it / kb_n);
+        const int64_t seg_end = (it_end < int64_t(tile + 1) * kb_n) ? it_end : int64_t(tile + 1) * kb_n;
+        if (!mbar_wait(acc_empty, acc_phase ^ 1u, abort_flag, p.status)) break;
+        tc_fence_after();
+        bool first = true;
+        for (; it < seg_end; ++it) {
+          if (!mbar_wait(&conv[stage], phase, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(a_hi(stage)), al = smem_u32(a_lo(stage));
+          const uint32_t bh = smem_u32(b_hi(stage)), bl = smem_u32(b_lo(stage));
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t dbh = sw128_desc(bh + kk * 32, 16, 1024);
+            const uint64_t dbl = sw128_desc(bl + kk * 32, 16, 1024);
+            const uint64_t dah = sw128_desc(ah + kk * 32, 16, 1024);
+            const uint64_t dal = sw128_desc(al + kk * 32, 16, 1024);
+            umma_tf32(tmem_base, dah, dbh, kIdesc, (first && kk == 0) ? 0u : 1u);
+            umma_tf32(tmem_base, dah, dbl, kIdesc, 1u);
+            umma_tf32(tmem_base, dal, dbh, kIdesc, 1u);
+          }
+          first = false;
+          umma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(acc_full);
+        acc_phase ^= 1u;
+      }
+      umma_commit(drain);
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else if (warp >= 6) {
+    // converters: A tile -> hi (in place) and lo
+    const int ct = threadIdx.x - 6 * 32;  // 0..127
+    uint32_t stage = 0, phase = 0;
+    for (int64_t it = it_begin; it < it_end; ++it) {
+      if (!mbar_wait_warp(&full[stage], phase, abort_flag, p.status)) break;
+      if (MODE == 0) {
+        // K-major tile as loaded: split in place, elementwise
+        float4* hi = reinterpret_cast<float4*>(a_hi(stage));
+        float4* lo = reinterpret_cast<float4*>(a_lo(stage));
+#pragma unroll 4
+        for (int i = ct; i < int(C::kABytes / 16); i += 128) {
+          float4 v = hi[i], h, l;
+          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          l.x = v.x - h.x;
+          l.y = v.y - h.y;
+          l.z = v.z - h.z;
+          l.w = v.w - h.w;
+          hi[i] = h;
+          lo[i] = l;
+        }
+      } else {
+        // Co-range: the tile arrives as 4 boxes of [32 K-rows x 32 M-cols]
+        // (K = rows of A), 4 KB each.  Box hb holds output rows
+        // M = 32 hb .. 32 hb + 31, and those rows of the K-major operand
+        // occupy the same 4 KB, so converter warp hb transposes box hb in
+        // place: lane mc gathers the 32 K values of column mc (the warp reads
+        // one 128-byte source row per step, conflict-free), then writes row
+        // M = 32 hb + mc of hi in place and of lo into the twin buffer, in
+        // the 128-byte-swizzled K-major layout the MMA reads.
+        const float* src = reinterpret_cast<const float*>(a_hi(stage));
+        const int mm = ct, hb = mm >> 5, mc = mm & 31;
+        float v[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          v[k] = src[(hb * 4096 + k * 128 + ((((mc >> 2) ^ (k & 7)) << 4)) + ((mc & 3) << 2)) >> 2];
+        __syncwarp();
+        float* dhi = reinterpret_cast<float*>(a_hi(stage));
+        float* dlo = reinterpret_cast<float*>(a_lo(stage));
+#pragma unroll
+        for (int kc = 0; kc < 8; ++kc) {
+          float4 h, l;
+          h.x = __uint_as_float(__float_as_uint(v[4 * kc + 0]) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(v[4 * kc + 1]) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(v[4 * kc + 2]) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(v[4 * kc + 3]) & 0xFFFFE000u);
+          l.x = v[4 * kc + 0] - h.x;
+          l.y = v[4 * kc + 1] - h.y;
+          l.z = v[4 * kc + 2] - h.z;
+          l.w = v[4 * kc + 3] - h.w;
+          const int off = (mm * 128 + ((kc ^ (mm & 7)) << 4)) >> 2;
+          *reinterpret_cast<float4*>(dhi + off) = h;
+          *reinterpret_cast<float4*>(dlo + off) = l;
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[stage]);
+      if (++stage == STAGES) {
+        stage = 0;
+        phase ^= 1u;
+      }
+    }
+  } else {
+    // Epilogue: warps 2..5 own TMEM lane quarters (warp % 4).
+    const int q = warp & 3;
+    uint32_t acc_phase = 0;
+    int64_t it = it_begin;
+    while (it < it_end) {
+      const int tile = int(it / kb_n);
+      const int64_t seg_end = (it_end < int64_t(tile + 1) * kb_n) ? it_end : int64_t(tile + 1) * kb_n;
+      if (!mbar_wait_warp(acc_full, acc_phase, abort_flag, p.status)) break;
+      tc_fence_after();
+      const int64_t row = int64_t(tile) * 128 + q * 32 + lane;
+      const bool row_ok = row < p.m_out;
+      float* orow = p.out + row;
+#pragma unroll 1
+      for (int c0 = 0; c0 < NCOL; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem_base + (uint32_t(q * 32) << 16) + uint32_t(c0), v);
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < p.ell) atomicAdd(orow + int64_t(c0 + j) * p.ldo, v[j]);
+        }
+      }
+      tc_fence_before();
+      if (lane == 0) mbar_arrive(acc_empty);
+      acc_phase ^= 1u;
+      it = seg_end;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(C::kTmemCols));
+  }
+}
+
+__global__ void split_tf32_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ hi,
+                                  float* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols) {
+  const int64_t total = rows * cols;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i % rows, c = i / rows;
+    const float x = src[r + c * lds];
+    const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    hi[r + c * ldd] = h;
+    lo[r + c * ldd] = x - h;
   }
 }
 
@@ -415,6 +700,92 @@ void view_bf16(const ViewBf16Args& a, cudaStream_t s) {
       case 64: launch_ncol<1, 64>(ma, mb, p, tiles, sms, s); break;
       case 128: launch_ncol<1, 128>(ma, mb, p, tiles, sms, s); break;
       default: launch_ncol<1, 256>(ma, mb, p, tiles, sms, s); break;
+    }
+  }
+}
+
+
+namespace {
+CUtensorMap make_map_f32(const void* base, int64_t dim0, int64_t dim1, int64_t ld, int box0, int box1) {
+  LR_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, LR_ERR_ALIGNMENT, "TMA base not 16-byte aligned");
+  LR_REQUIRE((ld * 4) % 16 == 0, LR_ERR_ALIGNMENT, "TMA row stride not a multiple of 16 bytes");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {cuuint64_t(dim0), cuuint64_t(dim1)};
+  cuuint64_t strides[1] = {cuuint64_t(ld * 4)};
+  cuuint32_t box[2] = {cuuint32_t(box0), cuuint32_t(box1)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  LR_REQUIRE(r == CUDA_SUCCESS, LR_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
+  return m;
+}
+
+template <int MODE, int NCOL>
+void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMap& mbl, ViewParams p, int tiles,
+                 int sms, cudaStream_t s) {
+  constexpr int STAGES = (NCOL <= 64) ? 4 : (NCOL <= 128) ? 3 : 2;
+  using C = CfgT<MODE, NCOL, STAGES>;
+  auto kern = view_tf32x3_kernel<MODE, NCOL, STAGES>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  if (!attr_set[dev & 63]) {
+    LR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::kSmem)));
+    attr_set[dev & 63] = true;
+  }
+  p.iters_total = int64_t(tiles) * p.kblocks;
+  const int grid = int(std::min<int64_t>(sms, p.iters_total));
+  if (grid <= 0) return;
+  kern<<<grid, kThreadsT, C::kSmem, s>>>(ma, mbh, mbl, p);
+  LR_LAUNCH_CHECK();
+}
+}  // namespace
+
+void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd, int64_t rows, int64_t cols,
+                cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  const int grid = int(std::min<int64_t>(4096, (rows * cols + 255) / 256));
+  split_tf32_kernel<<<grid, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols);
+  LR_LAUNCH_CHECK();
+}
+
+void view_tf32x3(const ViewTf32Args& a, cudaStream_t s) {
+  LR_REQUIRE(a.ell >= 1 && a.ell <= 256, LR_ERR_UNSUPPORTED, "tf32 view handles ell <= 256 per call");
+  if (a.rows <= 0 || a.n <= 0) return;
+  const int sms = dev_info(a.device).sms;
+  const float* abase = a.A + a.row0 * a.lda;
+  ViewParams p{};
+  p.ell = a.ell;
+  p.out = a.out;
+  p.ldo = a.ldo;
+  p.status = a.status;
+  const int ncol = view_bf16_ncol(a.ell);
+  if (a.mode == 0) {
+    CUtensorMap ma = make_map_f32(abase, a.n, a.rows, a.lda, 32, 128);
+    CUtensorMap mh = make_map_f32(a.Bhi, a.n, a.ell, a.ldb, 32, ncol);
+    CUtensorMap ml = make_map_f32(a.Blo, a.n, a.ell, a.ldb, 32, ncol);
+    p.m_out = a.rows;
+    p.kblocks = ceil_div(a.n, 32);
+    const int tiles = ceil_div(a.rows, 128);
+    switch (ncol) {
+      case 32: launch_tf32<0, 32>(ma, mh, ml, p, tiles, sms, s); break;
+      case 64: launch_tf32<0, 64>(ma, mh, ml, p, tiles, sms, s); break;
+      case 128: launch_tf32<0, 128>(ma, mh, ml, p, tiles, sms, s); break;
+      default: launch_tf32<0, 256>(ma, mh, ml, p, tiles, sms, s); break;
+    }
+  } else {
+    CUtensorMap ma = make_map_f32(abase, a.n, a.rows, a.lda, 32, 32);
+    CUtensorMap mh = make_map_f32(a.Bhi, a.rows, a.ell, a.ldb, 32, ncol);
+    CUtensorMap ml = make_map_f32(a.Blo, a.rows, a.ell, a.ldb, 32, ncol);
+    p.m_out = a.n;
+    p.kblocks = ceil_div(a.rows, 32);
+    const int tiles = ceil_div(a.n, 128);
+    switch (ncol) {
+      case 32: launch_tf32<1, 32>(ma, mh, ml, p, tiles, sms, s); break;
+      case 64: launch_tf32<1, 64>(ma, mh, ml, p, tiles, sms, s); break;
+      case 128: launch_tf32<1, 128>(ma, mh, ml, p, tiles, sms, s); break;
+      default: launch_tf32<1, 256>(ma, mh, ml, p, tiles, sms, s); break;
     }
   }
 }

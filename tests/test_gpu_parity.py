@@ -257,6 +257,8 @@ def test_host_streamed_single_pass_matches_device_and_oracle(panel):
     u, s, vv = api().single_pass_host(ah, k, torch.tensor(om), torch.tensor(ps), panel_cols=panel)
     assert_status_ok()
     ud, sd, vd = api().single_pass(t32(a32), k, t32(om), t32(ps))
-    assert np.abs(f64(s) - f64(sd)).max() / f64(sd)[0] < 1e-6
+    # both are FP32 runs whose sketches sum the panels in different orders
+    # (atomic partial tiles), so they agree to the FP32 bar, not bitwise
+    assert np.abs(f64(s) - f64(sd)).max() / f64(sd)[0] < 1e-5
     uo, so, vo = Al.single_pass(a32.astype(np.float64), om.astype(np.float64), ps.astype(np.float64), k)
     print(check_tsvd(a32.astype(np.float64), u, s, vv, uo, so, vo))
