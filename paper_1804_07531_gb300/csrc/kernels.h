@@ -93,11 +93,12 @@ void f64_to_f32(const double* src, int lds, float* dst, int ldd, int rows, int c
 //   M = U diag(S) V^T; U overwrites Wk (rows x cols), V (cols x cols), S desc.
 void jacobi_svd(const float* M, int ldm, int rows, int cols, float* Wk, int ldw, float* V, int ldv, float* S,
                 double* S64, int* status, cudaStream_t s);
-// Cluster variant for square n x n (rows split over <= 8 CTAs); size 0 when
-// n does not fit.
+// Cluster variant for square n x n (rows of W and V split over the P CTAs of
+// a cluster, G lanes per column pair; 0 = the defaults); size 0 when n does
+// not fit.
 int jacobi_cluster_size(int n);
 void jacobi_svd_cluster(const float* M, int ldm, int n, float* U, int ldu, float* V, int ldv, float* S, int* status,
-                        cudaStream_t s);
+                        cudaStream_t s, int P = 0, int G = 0);
 // Copy a square FP64 upper-triangular R into FP32 (transposed if trans).
 void r_to_f32(const double* R, int ldr, int n, float* out, int ldo, bool trans, cudaStream_t s);
 // Small dense QR helper for the single-pass core: see single_pass driver.
