@@ -58,10 +58,30 @@ struct ViewTf32Args {
   float* out = nullptr;
   int64_t ldo = 0;
   int* status = nullptr;
+  const int* run_if = nullptr;  // device flag: the launch is a no-op when *run_if == 0
 };
 void view_tf32x3(const ViewTf32Args& a, cudaStream_t s);
+// C64 (a x b, ld ldc) += P^T Q for tall FP32 panels P (m x a, ld lda) and Q
+// (m x b, ld ldb), both col-major, on the tensor cores (3xTF32, both operands
+// split in shared memory; FP32 partial sums per CTA, added in FP64).  lda,
+// ldb multiples of 4 and 16-byte aligned bases (TMA).
+struct GramTf32Args {
+  int device = 0;
+  const float* P = nullptr;
+  int64_t lda = 0;
+  int a = 0;
+  const float* Q = nullptr;
+  int64_t ldb = 0;
+  int b = 0;
+  int64_t m = 0;
+  double* C64 = nullptr;
+  int64_t ldc = 0;
+  int* status = nullptr;
+  const int* run_if = nullptr;
+};
+void gram_tf32x3(const GramTf32Args& a, cudaStream_t s);
 void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd, int64_t rows, int64_t cols,
-                cudaStream_t s);
+                cudaStream_t s, float scale = 1.f);
 
 // ---------------------------------------------------------- elementwise
 void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s);

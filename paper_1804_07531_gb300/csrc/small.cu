@@ -87,177 +87,6 @@ __global__ void fix_signs_kernel(float* U, int64_t ldu, int64_t m, float* V, int
 }
 
 // Upper-triangular inverse of R (n x n, column-major FP32 in smem, lda n):
-// X = R^{-1} row by row from the bottom: X(i,i) = 1/R(i,i),
-// X(i,j) = -(sum_{k=i+1..j} R(i,k) X(k,j)) / R(i,i) for j > i.
-// Rows are processed in decreasing i; the n-i entries of row i are computed
-// in parallel, each dot product split over 8 threads.
-__device__ void upper_inverse_smem(const float* R, float* X, int n) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int idx = tid; idx < n * n; idx += nt) X[idx] = 0.f;
-  __syncthreads();
-  for (int i = n - 1; i >= 0; --i) {
-    const float rii = R[i + i * n];
-    // (n - i) outputs, 8 threads each; the loop trip count is the same for
-    // every thread so whole warps execute the shuffles.
-    const int work = (n - i) * 8;
-    for (int t0 = 0; t0 < work; t0 += nt) {
-      const int t = t0 + tid;
-      const bool act = t < work;
-      const int j = i + t / 8, part = t % 8;
-      float acc = 0.f;
-      if (act)
-        for (int k = i + 1 + part; k <= j; k += 8) acc = fmaf(R[i + k * n], X[k + j * n], acc);
-      acc += __shfl_down_sync(0xffffffffu, acc, 4, 8);
-      acc += __shfl_down_sync(0xffffffffu, acc, 2, 8);
-      acc += __shfl_down_sync(0xffffffffu, acc, 1, 8);
-      if (act && part == 0) X[i + j * n] = (j == i) ? 1.f / rii : -acc / rii;
-    }
-    __syncthreads();
-  }
-}
-
-// Cholesky G = R^T R (G FP64 in global, computed in FP32 in shared memory),
-// then Rinv = R^{-1} and Racc <- R Racc (or Racc = R when init).
-// Shared memory: 3 n x n FP32 matrices (n <= 128 -> 192 KB).
-//
-// mode: CHOL_PLAIN       plain Cholesky (a non-positive pivot is a breakdown);
-//       CHOL_SHIFT_IF_NEEDED  plain first; on breakdown retry with the shift of
-//                         shifted CholeskyQR (Fukaya et al. 2020) and set
-//                         *needs_more = 1 so the caller's optional pass runs;
-//       CHOL_IF_FLAGGED  run only when *needs_more != 0 (else write nothing).
-// The elimination keeps unscaled Schur complements (A(i,c) -= A(i,j) A(c,j) /
-// d_j with pivot d_j), so each column costs one barrier; L(i,j) =
-// A(i,j) / sqrt(d_j) is formed at the end.
-__device__ bool chol_smem(float* A, int n, float shift, int tid, int nt) {
-  for (int idx = tid; idx < n; idx += nt) A[idx + idx * n] += shift;
-  __syncthreads();
-  const int tx = tid & 31, ty = tid >> 5;
-  for (int j = 0; j < n; ++j) {
-    const float d = A[j + j * n];
-    if (!(d > 0.f) || !isfinite(d)) return false;  // same decision in every thread
-    const float inv = 1.f / d;
-    for (int c = j + 1 + ty; c < n; c += 32) {
-      const float acj = A[c + j * n] * inv;
-      for (int i = c + tx; i < n; i += 32) A[i + c * n] -= A[i + j * n] * acj;
-    }
-    __syncthreads();
-  }
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int r = idx % n, c = idx / n;
-    if (r > c) A[idx] /= sqrtf(A[c + c * n]);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < n; idx += nt) A[idx + idx * n] = sqrtf(A[idx + idx * n]);
-  __syncthreads();
-  return true;
-}
-
-__global__ void __launch_bounds__(1024) chol_inv_kernel(const double* __restrict__ G, int n, float* Rinv, int ldr,
-                                                        double* Racc, int ldacc, int init_acc, int mode,
-                                                        int* needs_more, int* status) {
-  extern __shared__ float sm[];
-  float* L = sm;            // lower Cholesky factor L = R^T, col-major n x n
-  float* X = sm + n * n;    // R^{-1}
-  float* T = X + n * n;     // scratch (R as upper, col-major)
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (mode == CHOL_IF_FLAGGED && (needs_more == nullptr || *needs_more == 0)) return;
-  __shared__ int nonfinite;
-  if (tid == 0) nonfinite = 0;
-  __syncthreads();
-  double tr_part = 0.0;
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int r = idx % n, c = idx / n;
-    const double g = G[idx];
-    if (!isfinite(g)) nonfinite = 1;
-    L[idx] = (r >= c) ? float(g) : 0.f;
-    if (r == c) tr_part += g;
-  }
-  __syncthreads();
-  if (nonfinite) {
-    if (tid == 0) set_status(status, LR_ERR_NONFINITE);
-    return;
-  }
-  bool ok = chol_smem(L, n, 0.f, tid, nt);
-  if (!ok && mode == CHOL_SHIFT_IF_NEEDED) {
-    // trace(G) as the norm estimate; the shift sits above the FP32 Gram and
-    // Cholesky rounding level, so the factorisation cannot break down.
-    __shared__ double tr;
-    if (tid == 0) tr = 0.0;
-    __syncthreads();
-    atomicAdd(&tr, tr_part);
-    for (int idx = tid; idx < n * n; idx += nt) {
-      const int r = idx % n, c = idx / n;
-      L[idx] = (r >= c) ? float(G[idx]) : 0.f;
-    }
-    __syncthreads();
-    ok = chol_smem(L, n, float(1e-5 * tr), tid, nt);
-    if (ok && tid == 0 && needs_more) *needs_more = 1;
-  }
-  if (!ok) {
-    if (tid == 0) set_status(status, LR_ERR_BREAKDOWN);
-    // leave a harmless identity so later kernels stay finite
-    for (int idx = tid; idx < n * n; idx += nt) {
-      const int r = idx % n, c = idx / n;
-      Rinv[r + c * ldr] = (r == c) ? 1.f : 0.f;
-    }
-    return;
-  }
-  // T = R = L^T (upper)
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int r = idx % n, c = idx / n;
-    T[idx] = (r <= c) ? L[c + r * n] : 0.f;
-  }
-  __syncthreads();
-  upper_inverse_smem(T, X, n);
-  for (int idx = tid; idx < n * n; idx += nt) {
-    const int r = idx % n, c = idx / n;
-    Rinv[r + c * ldr] = X[idx];
-  }
-  if (Racc) {
-    if (init_acc) {
-      for (int idx = tid; idx < n * n; idx += nt) {
-        const int r = idx % n, c = idx / n;
-        Racc[r + c * ldacc] = double(T[idx]);
-      }
-    } else {
-      // L <- Racc (FP32 copy), then Racc = T * L (both upper)
-      __syncthreads();
-      for (int idx = tid; idx < n * n; idx += nt) {
-        const int r = idx % n, c = idx / n;
-        L[idx] = (r <= c) ? float(Racc[r + c * ldacc]) : 0.f;
-      }
-      __syncthreads();
-      const int tx = tid & 31, ty = tid >> 5;
-      for (int c = ty; c < n; c += 32)
-        for (int r = tx; r < n; r += 32) {
-          float acc = 0.f;
-          if (r <= c)
-            for (int k = r; k <= c; ++k) acc = fmaf(T[r + k * n], L[k + c * n], acc);
-          Racc[r + c * ldacc] = double(acc);
-        }
-    }
-  }
-}
-
-// Inverse of an upper-triangular FP64 R (n x n, n <= 128) into FP32.
-__global__ void __launch_bounds__(1024) tri_inv_kernel(const double* __restrict__ R, int ldr, int n, float* X,
-                                                       int ldx, int* status) {
-  extern __shared__ float sm[];
-  float* T = sm;
-  float* Y = sm + n * n;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int r = idx % n, c = idx / n;
-    T[idx] = (r <= c) ? float(R[r + c * ldr]) : 0.f;
-    if (r == c && !(T[idx] != 0.f)) set_status(status, LR_ERR_BREAKDOWN);
-  }
-  __syncthreads();
-  upper_inverse_smem(T, Y, n);
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int r = idx % n, c = idx / n;
-    X[r + c * ldx] = Y[idx];
-  }
-}
-
 __global__ void add_block_kernel(double* R, int ldr, int r0, int c0, const double* C, int ldc, int rows, int cols) {
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * cols; idx += gridDim.x * blockDim.x) {
     const int r = idx % rows, c = idx / rows;
@@ -515,34 +344,6 @@ void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t ro
 void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n, int k, cudaStream_t s) {
   if (k <= 0) return;
   fix_signs_kernel<<<k, 256, 0, s>>>(U, ldu, m, V, ldv, n);
-  LR_LAUNCH_CHECK();
-}
-
-void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int mode,
-              int* needs_more, int* status, cudaStream_t s) {
-  LR_REQUIRE(ell >= 1 && ell <= 128, LR_ERR_UNSUPPORTED, "chol_inv: block width must be <= 128");
-  const size_t smem = size_t(3) * ell * ell * sizeof(float);
-  static bool attr[64] = {};
-  int dev = 0;
-  LR_CHECK_CUDA(cudaGetDevice(&dev));
-  if (!attr[dev & 63]) {
-    LR_CHECK_CUDA(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * 128 * 128 * 4));
-    attr[dev & 63] = true;
-  }
-  chol_inv_kernel<<<1, 1024, smem, s>>>(G, ell, Rinv, ldr, Racc, ldacc, init_acc ? 1 : 0, mode, needs_more, status);
-  LR_LAUNCH_CHECK();
-}
-
-void tri_inv(const double* R, int ldr, int n, float* X, int ldx, int* status, cudaStream_t s) {
-  LR_REQUIRE(n >= 1 && n <= 128, LR_ERR_UNSUPPORTED, "tri_inv: n must be <= 128");
-  static bool attr[64] = {};
-  int dev = 0;
-  LR_CHECK_CUDA(cudaGetDevice(&dev));
-  if (!attr[dev & 63]) {
-    LR_CHECK_CUDA(cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 128 * 128 * 4));
-    attr[dev & 63] = true;
-  }
-  tri_inv_kernel<<<1, 1024, size_t(2) * n * n * sizeof(float), s>>>(R, ldr, n, X, ldx, status);
   LR_LAUNCH_CHECK();
 }
 

@@ -158,8 +158,10 @@ struct ViewParams {
   int kblocks;          // ceil(K / 64)
   int64_t iters_total;  // tiles * kblocks
   float* out;
+  double* out64;        // FP64 output (products accumulated in FP64 across CTAs)
   int64_t ldo;
   int* status;
+  const int* run_if;    // the launch is a no-op when *run_if == 0
 };
 
 template <int MODE, int NS, int NCOL, int STAGES>
@@ -364,10 +366,15 @@ struct CfgT {
   static_assert(NCOL % 16 == 0 && NCOL >= 16 && NCOL <= 256, "M=128 MMA needs N % 16 == 0, N <= 256");
 };
 
-template <int MODE, int NCOL, int STAGES>
+// SPLITB: the thin operand arrives raw (one FP32 tile through tmBhi) and the
+// converter warps split it in shared memory as well; OUT64: the partial
+// products are added into an FP64 output.  Both serve the tall-skinny
+// products of the thin QR (Grams P^T Q of long FP32 panels).
+template <int MODE, int NCOL, int STAGES, bool SPLITB, bool OUT64>
 __global__ void __launch_bounds__(kThreadsT, 1)
     view_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBhi,
                        const __grid_constant__ CUtensorMap tmBlo, ViewParams p) {
+  if (p.run_if && *p.run_if == 0) return;
   using C = CfgT<MODE, NCOL, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -422,7 +429,7 @@ __global__ void __launch_bounds__(kThreadsT, 1)
         const int tile = int(it / kb_n);
         const int kb = int(it % kb_n);
         if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.status)) break;
-        mbar_expect_tx(&full[stage], C::kABytes + 2 * C::kBBytes);
+        mbar_expect_tx(&full[stage], C::kABytes + (SPLITB ? 1u : 2u) * C::kBBytes);
         if (MODE == 0) {
           tma_load_2d(a_hi(stage), &tmA, &full[stage], kb * 32, tile * 128);
         } else {
@@ -430,7 +437,7 @@ __global__ void __launch_bounds__(kThreadsT, 1)
           for (int h = 0; h < 4; ++h) tma_load_2d(a_hi(stage) + h * 4096, &tmA, &full[stage], tile * 128 + h * 32, kb * 32);
         }
         tma_load_2d(b_hi(stage), &tmBhi, &full[stage], kb * 32, 0);
-        tma_load_2d(b_lo(stage), &tmBlo, &full[stage], kb * 32, 0);
+        if (!SPLITB) tma_load_2d(b_lo(stage), &tmBlo, &full[stage], kb * 32, 0);
         if (++stage == STAGES) {
           stage = 0;
           phase ^= 1u;
@@ -546,6 +553,25 @@ __global__ void __launch_bounds__(kThreadsT, 1)
           *reinterpret_cast<float4*>(dlo + off) = l;
         }
       }
+      if (SPLITB) {
+        // the thin operand's tile is K-major as loaded: split in place
+        float4* hi = reinterpret_cast<float4*>(b_hi(stage));
+        float4* lo = reinterpret_cast<float4*>(b_lo(stage));
+#pragma unroll 4
+        for (int i = ct; i < int(C::kBBytes / 16); i += 128) {
+          float4 v = hi[i], h, l;
+          h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+          l.x = v.x - h.x;
+          l.y = v.y - h.y;
+          l.z = v.z - h.z;
+          l.w = v.w - h.w;
+          hi[i] = h;
+          lo[i] = l;
+        }
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&conv[stage]);
@@ -566,7 +592,6 @@ __global__ void __launch_bounds__(kThreadsT, 1)
       tc_fence_after();
       const int64_t row = int64_t(tile) * 128 + q * 32 + lane;
       const bool row_ok = row < p.m_out;
-      float* orow = p.out + row;
 #pragma unroll 1
       for (int c0 = 0; c0 < NCOL; c0 += 16) {
         float v[16];
@@ -574,7 +599,10 @@ __global__ void __launch_bounds__(kThreadsT, 1)
         if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (c0 + j < p.ell) atomicAdd(orow + int64_t(c0 + j) * p.ldo, v[j]);
+            if (c0 + j < p.ell) {
+              if (OUT64) atomicAdd(p.out64 + row + int64_t(c0 + j) * p.ldo, double(v[j]));
+              else atomicAdd(p.out + row + int64_t(c0 + j) * p.ldo, v[j]);
+            }
         }
       }
       tc_fence_before();
@@ -593,11 +621,11 @@ __global__ void __launch_bounds__(kThreadsT, 1)
 }
 
 __global__ void split_tf32_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ hi,
-                                  float* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols) {
+                                  float* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols, float scale) {
   const int64_t total = rows * cols;
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
     const int64_t r = i % rows, c = i / rows;
-    const float x = src[r + c * lds];
+    const float x = scale * src[r + c * lds];
     const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
     hi[r + c * ldd] = h;
     lo[r + c * ldd] = x - h;
@@ -721,12 +749,12 @@ CUtensorMap make_map_f32(const void* base, int64_t dim0, int64_t dim1, int64_t l
   return m;
 }
 
-template <int MODE, int NCOL>
+template <int MODE, int NCOL, bool SPLITB = false, bool OUT64 = false>
 void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMap& mbl, ViewParams p, int tiles,
                  int sms, cudaStream_t s) {
   constexpr int STAGES = (NCOL <= 64) ? 4 : (NCOL <= 128) ? 3 : 2;
   using C = CfgT<MODE, NCOL, STAGES>;
-  auto kern = view_tf32x3_kernel<MODE, NCOL, STAGES>;
+  auto kern = view_tf32x3_kernel<MODE, NCOL, STAGES, SPLITB, OUT64>;
   static bool attr_set[64] = {};
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
@@ -743,11 +771,36 @@ void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMa
 }  // namespace
 
 void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd, int64_t rows, int64_t cols,
-                cudaStream_t s) {
+                cudaStream_t s, float scale) {
   if (rows <= 0 || cols <= 0) return;
   const int grid = int(std::min<int64_t>(4096, (rows * cols + 255) / 256));
-  split_tf32_kernel<<<grid, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols);
+  split_tf32_kernel<<<grid, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, scale);
   LR_LAUNCH_CHECK();
+}
+
+void gram_tf32x3(const GramTf32Args& a, cudaStream_t s) {
+  LR_REQUIRE(a.b >= 1 && a.b <= 256, LR_ERR_UNSUPPORTED, "tensor-core Gram handles b <= 256 per call");
+  if (a.a <= 0 || a.m <= 0) return;
+  const int sms = dev_info(a.device).sms;
+  ViewParams p{};
+  p.ell = a.b;
+  p.out64 = a.C64;
+  p.ldo = a.ldc;
+  p.status = a.status;
+  p.run_if = a.run_if;
+  p.m_out = a.a;
+  p.kblocks = ceil_div(a.m, 32);
+  const int ncol = view_bf16_ncol(a.b);
+  // A = P^T (a x m row-major, row stride lda); B = Q (m x b col-major), raw
+  CUtensorMap ma = make_map_f32(a.P, a.m, a.a, a.lda, 32, 128);
+  CUtensorMap mb = make_map_f32(a.Q, a.m, a.b, a.ldb, 32, ncol);
+  const int tiles = ceil_div(a.a, 128);
+  switch (ncol) {
+    case 32: launch_tf32<0, 32, true, true>(ma, mb, mb, p, tiles, sms, s); break;
+    case 64: launch_tf32<0, 64, true, true>(ma, mb, mb, p, tiles, sms, s); break;
+    case 128: launch_tf32<0, 128, true, true>(ma, mb, mb, p, tiles, sms, s); break;
+    default: launch_tf32<0, 256, true, true>(ma, mb, mb, p, tiles, sms, s); break;
+  }
 }
 
 void view_tf32x3(const ViewTf32Args& a, cudaStream_t s) {
@@ -760,6 +813,7 @@ void view_tf32x3(const ViewTf32Args& a, cudaStream_t s) {
   p.out = a.out;
   p.ldo = a.ldo;
   p.status = a.status;
+  p.run_if = a.run_if;
   const int ncol = view_bf16_ncol(a.ell);
   if (a.mode == 0) {
     CUtensorMap ma = make_map_f32(abase, a.n, a.rows, a.lda, 32, 128);
