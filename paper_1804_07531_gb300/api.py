@@ -96,29 +96,33 @@ def _outs(a, k):
     return empty_cm(m, k, a.device), torch.empty(k, dtype=torch.float32, device=a.device), empty_cm(n, k, a.device)
 
 
-def subspace_iter(a, k, p, v, omega, shifted_fallback=False, stream=None):
-    """Alg. 2: generalized subspace iteration with v >= 2 views -> (U, S, V)."""
+def subspace_iter(a, k, p, v, omega, shifted_fallback=False, split_last=False, stream=None):
+    """Alg. 2: generalized subspace iteration with v >= 2 views -> (U, S, V).
+
+    split_last (BF16 A only): the last view's operand enters as two BF16
+    terms (hi + lo), so that view's products carry ~16 operand bits."""
     a, (omega,) = _prep(a, omega)
     h = Handle.get(a.device)
     m, n = a.shape
     h.reserve(m, n, k + p, 0, v)
     u, s, vv = _outs(a, k)
     mats = [mat_a(a), mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
-    o = _opts(shifted_fallback=shifted_fallback)
+    o = _opts(shifted_fallback=shifted_fallback, split_last=split_last)
     _call(h, lib().lr_subspace_iter, _p(mats[0]), k, p, v, _p(mats[1]), _p(mats[2]), _p(mats[3]),
           _p(mats[4]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return u, s, vv
 
 
-def block_krylov(a, k, p, v, omega, enhanced=False, shifted_fallback=False, stream=None):
-    """Alg. 9 (or the row-streamed variant of Section 7.3 with enhanced=True)."""
+def block_krylov(a, k, p, v, omega, enhanced=False, shifted_fallback=False, split_last=False, stream=None):
+    """Alg. 9 (or the row-streamed variant of Section 7.3 with enhanced=True);
+    split_last as in subspace_iter."""
     a, (omega,) = _prep(a, omega)
     h = Handle.get(a.device)
     m, n = a.shape
     h.reserve(m, n, k + p, 0, v)
     u, s, vv = _outs(a, k)
     mats = [mat_a(a), mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
-    o = _opts(enhanced=enhanced, shifted_fallback=shifted_fallback)
+    o = _opts(enhanced=enhanced, shifted_fallback=shifted_fallback, split_last=split_last)
     _call(h, lib().lr_block_krylov, _p(mats[0]), k, p, v, _p(mats[1]), _p(mats[2]), _p(mats[3]),
           _p(mats[4]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return u, s, vv

@@ -194,20 +194,26 @@ void gram64(Ctx& c, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
 // BF16 copy for a BF16 A, TF32 hi/lo split for an F32 A.
 struct SplitOp {
   const __nv_bfloat16* bf = nullptr;
+  const __nv_bfloat16* bf_lo = nullptr;  // BF16 remainder x - bf16(x) (split form), or null
   const float* hi = nullptr;
   const float* lo = nullptr;
   int64_t ld = 0;
 };
 
 // Converts the thin operand (rows x ell) into the form the view kernel of
-// A's precision reads.
-SplitOp convert_operand(Ctx& c, const AMat& A, const float* B, int64_t ldb, int64_t rows, int ell) {
+// A's precision reads.  With split (BF16 A only) the operand is also kept as
+// a second BF16 term, x = bf16(x) + bf16(x - bf16(x)) to ~2^-16 relative,
+// and the view adds both products.
+SplitOp convert_operand(Ctx& c, const AMat& A, const float* B, int64_t ldb, int64_t rows, int ell,
+                        bool split = false) {
   SplitOp o;
   if (A.bf16) {
     o.ld = round8(rows);
     auto* t = c.ar.take<__nv_bfloat16>(size_t(o.ld) * ell);
-    if (!c.measure) f32_to_bf16(B, ldb, t, nullptr, o.ld, rows, ell, c.s);
+    auto* t2 = split ? c.ar.take<__nv_bfloat16>(size_t(o.ld) * ell) : nullptr;
+    if (!c.measure) f32_to_bf16(B, ldb, t, t2, o.ld, rows, ell, c.s);
     o.bf = t;
+    o.bf_lo = t2;
   } else {
     o.ld = round4(rows);
     float* h = c.ar.take<float>(size_t(o.ld) * ell);
@@ -220,7 +226,7 @@ SplitOp convert_operand(Ctx& c, const AMat& A, const float* B, int64_t ldb, int6
 }
 
 void view_band(Ctx& c, const AMat& A, int mode, const float* B, int64_t ldb, int ell, float* out, int64_t ldo,
-               int64_t r0, int64_t rows, const SplitOp* pre = nullptr) {
+               int64_t r0, int64_t rows, const SplitOp* pre = nullptr, bool split = false) {
   if (rows <= 0) return;
   {
     ArenaScope sc(c.ar);
@@ -229,9 +235,10 @@ void view_band(Ctx& c, const AMat& A, int mode, const float* B, int64_t ldb, int
       op = *pre;
     } else {
       const int64_t orows = (mode == 0) ? A.n : rows;
-      op = convert_operand(c, A, mode == 0 ? B : B + r0, ldb, orows, ell);
+      op = convert_operand(c, A, mode == 0 ? B : B + r0, ldb, orows, ell, split);
       if (mode == 1) {  // converted from the band's rows: index from row 0
         if (op.bf) op.bf -= r0;
+        if (op.bf_lo) op.bf_lo -= r0;
         if (op.hi) {
           op.hi -= r0;
           op.lo -= r0;
@@ -258,6 +265,10 @@ void view_band(Ctx& c, const AMat& A, int mode, const float* B, int64_t ldb, int
         a.ldo = ldo;
         a.status = c.status;
         view_bf16(a, c.s);
+        if (op.bf_lo) {  // second term of the split operand, same accumulator
+          a.B = op.bf_lo + (mode == 1 ? r0 : 0) + int64_t(g0) * op.ld;
+          view_bf16(a, c.s);
+        }
       } else {
         ViewTf32Args a;
         a.device = c.h->device;
@@ -294,15 +305,16 @@ int64_t band_rows(const AMat& A, int band_mb) {
   return std::min<int64_t>(r, (A.m + 255) / 256 * 256);
 }
 
-// Y = A X (X: n x ell).
-void view_range(Ctx& c, const AMat& A, const Mat& X, Mat Y) {
+// Y = A X (X: n x ell).  last: the schedule's final view, whose operand is
+// split in two BF16 terms when opts.split_last asks for it.
+void view_range(Ctx& c, const AMat& A, const Mat& X, Mat Y, bool last = false) {
   if (!c.measure) zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
-  view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, 0, A.m);
+  view_band(c, A, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, 0, A.m, nullptr, last && c.opt.split_last && A.bf16);
 }
 // Z = A^T W (W: m x ell).
-void view_corange(Ctx& c, const AMat& A, const Mat& W, Mat Z) {
+void view_corange(Ctx& c, const AMat& A, const Mat& W, Mat Z, bool last = false) {
   if (!c.measure) zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
-  view_band(c, A, 1, W.p, W.ld, int(W.cols), Z.p, Z.ld, 0, A.m);
+  view_band(c, A, 1, W.p, W.ld, int(W.cols), Z.p, Z.ld, 0, A.m, nullptr, last && c.opt.split_last && A.bf16);
 }
 
 // Y = A X and Z = A^T W (the two sketches of Alg. 7).  The operands are
@@ -371,6 +383,7 @@ void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
   double* G64 = c.ar.take<double>(size_t(std::max(L, wmax)) * wmax);
   float* C32 = c.ar.take<float>(size_t(L) * wmax);
   float* Rinv = c.ar.take<float>(size_t(wmax) * wmax);
+  double* R2 = c.ar.take<double>(size_t(wmax) * wmax);  // factor of a later pass
   int* flags = c.ar.take<int>(size_t(nb));
   if (c.measure) return;
   TraceScope tr(c, LR_TRACE_ORTH);
@@ -400,13 +413,15 @@ void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w);
     chol_inv(G64, w, Rinv, w, Rbb, L, true, CHOL_SHIFT_IF_NEEDED, more, c.status, c.s);
     gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m);
-    // pass 2: T -> Y_b
+    // pass 2: T -> Y_b (R_bb <- R_2 R_bb by a separate many-CTA product)
     gram64(c, w, w, m, T, m, T, m, G64, w);
-    chol_inv(G64, w, Rinv, w, Rbb, L, false, CHOL_PLAIN, more, c.status, c.s);
+    chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_PLAIN, more, c.status, c.s);
+    if (Rbb) upper_product(R2, w, Rbb, L, w, nullptr, c.s);
     gemm(c, m, w, w, false, T, m, false, Rinv, w, Yb, Y.ld);
     // pass 3 (only after a shifted pass 1): Y_b -> T -> Y_b
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w, more);
-    chol_inv(G64, w, Rinv, w, Rbb, L, false, CHOL_IF_FLAGGED, more, c.status, c.s);
+    chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_IF_FLAGGED, more, c.status, c.s);
+    if (Rbb) upper_product(R2, w, Rbb, L, w, more, c.s);
     gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m, 1.f, 0.f, more);
     copy_f32(T, m, Yb, Y.ld, m, w, c.s, more);
     c0 += w;
@@ -489,11 +504,11 @@ void run_subspace(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, O
   Mat cur = Om;  // Q_r = Omega (Alg. 2 starts from the raw Gaussian)
   for (int j = 1; j <= v; ++j) {
     if (j % 2 == 1) {
-      view_range(c, A, cur, Qc);       // A Q_r
-      orth(c, Qc, Rc);                 // [Q_c, R_c] = qr(A Q_r)
+      view_range(c, A, cur, Qc, j == v);    // A Q_r
+      orth(c, Qc, Rc);                      // [Q_c, R_c] = qr(A Q_r)
     } else {
-      view_corange(c, A, Qc, Qr);      // A^T Q_c
-      orth(c, Qr, Rr);                 // [Q_r, R_r] = qr(A^T Q_c)
+      view_corange(c, A, Qc, Qr, j == v);   // A^T Q_c
+      orth(c, Qr, Rr);                      // [Q_r, R_r] = qr(A^T Q_c)
       cur = Qr;
     }
   }
@@ -536,12 +551,12 @@ void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Out
   }
   orth(c, K, nullptr, true);             // Q = qr(K)
   if (even) {
-    view_corange(c, A, K, F);            // A^T Q_c
+    view_corange(c, A, K, F, true);      // A^T Q_c
     orth(c, F, Rf);                      // [Q_r, R_r]
     core_svd(c, Rf, Lk, W, Vj, Sv);      // R_r = V^ L U^T
     write_outputs(c, K, Vj, F, W, Lk, Sv, k, o);
   } else {
-    view_range(c, A, K, F);              // A Q_r
+    view_range(c, A, K, F, true);        // A Q_r
     orth(c, F, Rf);                      // [Q_c, R_c]
     core_svd(c, Rf, Lk, W, Vj, Sv);      // R_c = U^ L V^T
     write_outputs(c, F, W, K, Vj, Lk, Sv, k, o);
@@ -575,7 +590,7 @@ void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat&
     x = blk;
   }
   orth(c, K, nullptr, true);             // Q_r = qr(K_r)
-  view_range(c, A, K, F);                // last view: A Q_r
+  view_range(c, A, K, F, true);          // last view: A Q_r
   orth(c, F, Rf);
   core_svd(c, Rf, Lk, W, Vj, Sv);        // R_c = U^ L V^T
   write_outputs(c, F, W, K, Vj, Lk, Sv, k, o);
@@ -984,6 +999,7 @@ lr_status lr_workspace_size(lr_handle h, int64_t m, int64_t n, int ell1, int ell
         c.ar.measure = true;
         c.sms = 1;
         c.opt.shifted_fallback = 1;
+        c.opt.split_last = 1;  // size for the split form too
         try {
           body(c);
         } catch (const Error&) {

@@ -63,26 +63,32 @@ __device__ __forceinline__ float dot4(const float* a, int sa, const float* b, in
 }
 
 // Factors the symmetric block at (k0, k0) of A (lower part used) as L L^T in
-// registers -- lane i holds row i; column j's multipliers are broadcast by
-// shuffles -- and writes the rows of L_kk (zeros above the diagonal) to L.
-// Returns false in every lane on a pivot that is not positive and finite.
-__device__ __noinline__ bool warp_factor_block(const float* A, float* L, int ld, int k0, int lane) {
+// registers -- lane i holds row i -- and writes the rows of L_kk (zeros above
+// the diagonal) to L.  Column j of the factor is broadcast through shared
+// memory (col, 32 floats): one store per lane, then independent loads, so
+// the loads of a step overlap instead of serialising like a chain of warp
+// shuffles.  Returns false in every lane on a pivot that is not positive and
+// finite.
+__device__ __noinline__ bool warp_factor_block(const float* A, float* L, int ld, int k0, int lane, float* col) {
   float a[kB];
 #pragma unroll
   for (int c = 0; c < kB; ++c) a[c] = A[(k0 + lane) + (k0 + c) * ld];
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < kB; ++j) {
-    const float d = __shfl_sync(0xffffffffu, a[j], j);
+    // the pivot: lane j's updated diagonal entry
+    if (lane == j) col[32] = a[j];
+    __syncwarp();
+    const float d = col[32];
     ok = ok && (d > 0.f) && isfinite(d);
     const float dd = fmaxf(d, 1e-30f);
     const float inv = rsqrt_refined(dd);  // 1 / l_jj
     a[j] = (lane > j) ? a[j] * inv : (lane == j ? dd * inv : a[j]);
+    col[lane] = a[j];  // column j of L (entries below the diagonal used)
+    __syncwarp();
 #pragma unroll
-    for (int c = j + 1; c < kB; ++c) {
-      const float lcj = __shfl_sync(0xffffffffu, a[j], c);
-      a[c] = (lane >= c) ? fmaf(-a[j], lcj, a[c]) : a[c];
-    }
+    for (int c = j + 1; c < kB; ++c) a[c] = (lane >= c) ? fmaf(-a[j], col[c], a[c]) : a[c];
+    __syncwarp();
   }
 #pragma unroll
   for (int c = 0; c < kB; ++c) L[(k0 + lane) + (k0 + c) * ld] = (c <= lane) ? a[c] : 0.f;
@@ -111,13 +117,13 @@ __device__ __noinline__ void warp_invert_block(const float* L, float* X, int ld,
 // Blocked factorisation of the N x N matrix in A (lower part used): L and
 // the diagonal blocks of X = L^{-1}.  A is overwritten by Schur
 // complements.  Returns true (uniformly) on a non-positive pivot.
-__device__ __forceinline__ bool block_cholesky(float* A, float* L, float* X, int N, int ld, int* bad) {
+__device__ __forceinline__ bool block_cholesky(float* A, float* L, float* X, int N, int ld, int* bad, float* colbuf) {
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid / 32, lane = tid % 32;
   const int nb = N / kB;
   for (int k = 0; k < nb; ++k) {
     const int k0 = k * kB;
     if (warp == 0) {
-      const bool ok = warp_factor_block(A, L, ld, k0, lane);
+      const bool ok = warp_factor_block(A, L, ld, k0, lane, colbuf);
       __syncwarp();
       warp_invert_block(L, X, ld, k0, lane);
       if (lane == 0) *bad = ok ? 0 : 1;
@@ -185,6 +191,7 @@ __global__ void __launch_bounds__(kThreadsC) chol_inv_kernel(const double* __res
   float* X = L + N * ld;
   __shared__ int bad, nonfinite;
   __shared__ double tr;
+  __shared__ float colbuf[kB + 1];  // column broadcast of the warp factorisation
   const int tid = threadIdx.x, nt = blockDim.x;
   if (tid == 0) nonfinite = 0;
   if (tid < 32) {  // trace of G (the norm estimate for the shift)
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(kThreadsC) chol_inv_kernel(const double* __res
       }
       __syncthreads();
     }
-    broke = block_cholesky(A, L, X, N, ld, &bad);
+    broke = block_cholesky(A, L, X, N, ld, &bad, colbuf);
     if (!broke || mode != CHOL_SHIFT_IF_NEEDED) break;
   }
   if (!broke && shifted && tid == 0 && needs_more) *needs_more = 1;

@@ -312,7 +312,31 @@ __global__ void qr_bwd_sym_kernel(const float* M, const double* C, int n, float*
 
 inline int grid_for(int64_t total) { return int(std::min<int64_t>(4096, std::max<int64_t>(1, (total + 255) / 256))); }
 
+// Racc <- R2 Racc for upper-triangular n x n FP64 factors (Racc ld ldr,
+// R2 ld ld2): CTA c owns column c of Racc, staged in shared memory so the
+// column can be overwritten in place.  A no-op when *run_if == 0.
+__global__ void upper_product_kernel(const double* __restrict__ R2, int ld2, double* Racc, int ldr, int n,
+                                     const int* run_if) {
+  if (run_if && *run_if == 0) return;
+  extern __shared__ double colc[];
+  const int c = blockIdx.x;
+  for (int m = threadIdx.x; m <= c; m += blockDim.x) colc[m] = Racc[m + int64_t(c) * ldr];
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    double acc = 0.0;
+    if (r <= c)
+      for (int m = r; m <= c; ++m) acc = fma(R2[r + int64_t(m) * ld2], colc[m], acc);
+    Racc[r + int64_t(c) * ldr] = acc;
+  }
+}
+
 }  // namespace
+
+void upper_product(const double* R2, int ld2, double* Racc, int ldr, int n, const int* run_if, cudaStream_t s) {
+  if (n <= 0) return;
+  upper_product_kernel<<<n, 128, size_t(n) * sizeof(double), s>>>(R2, ld2, Racc, ldr, n, run_if);
+  LR_LAUNCH_CHECK();
+}
 
 void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return;

@@ -152,6 +152,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
 struct ViewParams {
   int64_t m_out;        // valid output rows
   int ell;              // valid output columns
@@ -354,14 +364,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 // co-range view the converter warps also transpose the staged tile (the
 // MN-major operand form the BF16 kernel uses for the co-range view gave
 // wrong products with TF32 operands on this GPU).
+//
+// Accumulation in chunks: the tensor core's FP32 accumulation into TMEM loses
+// a little in every MMA (measured: a bias of about -9e-8 of the result per
+// 32 K-elements, so -5e-5 at K = 20000), which would exceed the FP32 form's
+// error budget on long views.  The MMAs therefore accumulate at most
+// kChunkKb k-blocks (256 K-elements) in TMEM; the epilogue warps add each
+// chunk into a running sum kept in a second TMEM region with ordinary
+// round-to-nearest FP32 additions, and add the running sum into the output
+// at the end of the work segment.  The bias is then bounded by one chunk's.
 constexpr int kThreadsT = 320;  // TMA, MMA, 4 epilogue, 4 converter warps
+constexpr int kChunkKb = 8;     // k-blocks of 32 accumulated in TMEM per chunk
 
 template <int MODE, int NCOL, int STAGES>
 struct CfgT {
   static constexpr uint32_t kABytes = 16384u;            // 128 x 32 FP32
   static constexpr uint32_t kBBytes = NCOL * 128u;       // NCOL rows x 32 FP32
   static constexpr uint32_t kStage = 2 * kABytes + 2 * kBBytes;
-  static constexpr uint32_t kTmemCols = NCOL <= 32 ? 32 : NCOL <= 64 ? 64 : NCOL <= 128 ? 128 : 256;
+  // TMEM: the chunk accumulator (NCOL columns) and the running sum (NCOL)
+  static constexpr uint32_t kTmemCols = NCOL <= 16 ? 32 : NCOL <= 32 ? 64 : NCOL <= 64 ? 128 : NCOL <= 128 ? 256 : 512;
   static constexpr size_t kSmem = size_t(STAGES) * kStage + 1024 + 256;
   static_assert(NCOL % 16 == 0 && NCOL >= 16 && NCOL <= 256, "M=128 MMA needs N % 16 == 0, N <= 256");
 };
@@ -458,10 +479,11 @@ __global__ void __launch_bounds__(kThreadsT, 1)
       while (ok && it < it_end) {
         const int tile = int(it / kb_n);
         const int64_t seg_end = (it_end < int64_t(tile + 1) * kb_n) ? it_end : int64_t(tile + 1) * kb_n;
+        const int64_t chunk_end = (seg_end < it + kChunkKb) ? seg_end : it + kChunkKb;
         if (!mbar_wait(acc_empty, acc_phase ^ 1u, abort_flag, p.status)) break;
         tc_fence_after();
         bool first = true;
-        for (; it < seg_end; ++it) {
+        for (; it < chunk_end; ++it) {
           if (!mbar_wait(&conv[stage], phase, abort_flag, p.status)) {
             ok = false;
             break;
@@ -581,13 +603,18 @@ __global__ void __launch_bounds__(kThreadsT, 1)
       }
     }
   } else {
-    // Epilogue: warps 2..5 own TMEM lane quarters (warp % 4).
+    // Epilogue: warps 2..5 own TMEM lane quarters (warp % 4).  Per chunk:
+    // running (+)= chunk; at the segment's last chunk the sum goes out.
     const int q = warp & 3;
+    const uint32_t lane_base = tmem_base + (uint32_t(q * 32) << 16);
     uint32_t acc_phase = 0;
     int64_t it = it_begin;
+    bool first_chunk = true;
     while (it < it_end) {
       const int tile = int(it / kb_n);
       const int64_t seg_end = (it_end < int64_t(tile + 1) * kb_n) ? it_end : int64_t(tile + 1) * kb_n;
+      const int64_t chunk_end = (seg_end < it + kChunkKb) ? seg_end : it + kChunkKb;
+      const bool last_chunk = chunk_end == seg_end;
       if (!mbar_wait_warp(acc_full, acc_phase, abort_flag, p.status)) break;
       tc_fence_after();
       const int64_t row = int64_t(tile) * 128 + q * 32 + lane;
@@ -595,8 +622,16 @@ __global__ void __launch_bounds__(kThreadsT, 1)
 #pragma unroll 1
       for (int c0 = 0; c0 < NCOL; c0 += 16) {
         float v[16];
-        tmem_ld16(tmem_base + (uint32_t(q * 32) << 16) + uint32_t(c0), v);
-        if (row_ok) {
+        tmem_ld16(lane_base + uint32_t(c0), v);
+        if (!first_chunk) {
+          float r[16];
+          tmem_ld16(lane_base + uint32_t(NCOL + c0), r);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] += r[j];
+        }
+        if (!last_chunk) {
+          tmem_st16(lane_base + uint32_t(NCOL + c0), v);
+        } else if (row_ok) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
             if (c0 + j < p.ell) {
@@ -605,10 +640,12 @@ __global__ void __launch_bounds__(kThreadsT, 1)
             }
         }
       }
+      if (!last_chunk) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       tc_fence_before();
       if (lane == 0) mbar_arrive(acc_empty);
       acc_phase ^= 1u;
-      it = seg_end;
+      first_chunk = last_chunk;
+      it = chunk_end;
     }
   }
 

@@ -1,0 +1,124 @@
+"""GPU parity at the workloads' full sizes.
+
+The block-Krylov workload runs exactly as the benchmark times it (same seeded
+inputs and sizes, same entry point).  The FP64 oracle cannot run that
+workload in seconds, so it is checked on sampled outputs the oracle-side
+arithmetic computes one by one and on properties that hold at any size:
+  * views: sampled rows of Y = A X and of Z = A^T W against FP64 products of
+    the same BF16 values;
+  * the factorisation: A^T U = V diag(s) holds exactly for the outputs of
+    Alg. 9 with an even number of views (U = Q_c U^, V = Q_r V^ and
+    Q_r R_r = A^T Q_c with R_r = V^ L U^^T), checked on sampled columns of A;
+    U and V orthonormal; s descending and, for this spectrum with k + p = 120
+    and v = 4, within the BF16 rounding of A of the known sigma_j = j^-1.5.
+The single-pass workload (20000 x 10000) is compared with the FP64 oracle in
+full, at the FP32 tolerances of the other parity tests.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import algorithms as Al  # noqa: E402
+from paper_1804_07531_gb300 import synth as S  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def api():
+    from paper_1804_07531_gb300 import api as _api
+    return _api
+
+
+def f64(t):
+    return t.detach().double().cpu().numpy()
+
+
+def assert_status_ok():
+    st = api().device_status(0)
+    assert st == 0, f"device status {st}"
+
+
+@pytest.fixture(scope="module")
+def krylov_workload():
+    import bench
+    a, omega = bench.make_inputs(torch.device(DEV))
+    yield a, omega
+    del a, omega
+    torch.cuda.empty_cache()
+
+
+def test_fullsize_views_sampled_rows(krylov_workload):
+    a, omega = krylov_workload
+    m, n = a.shape
+    gen = torch.Generator(device=DEV)
+    gen.manual_seed(5)
+    w = torch.randn(m, 240, generator=gen, device=DEV)
+    y, z = api().sketch(a, omega, w)
+    assert_status_ok()
+    rng = np.random.default_rng(6)
+    rows = rng.choice(m, 64, replace=False)
+    cols = rng.choice(n, 64, replace=False)
+    xb = omega.bfloat16().double().cpu().numpy()   # the operand as the kernel sees it
+    wb = w.bfloat16().double().cpu().numpy()
+    a_rows = a[torch.tensor(rows, device=DEV)].double().cpu().numpy()
+    a_cols = a[:, torch.tensor(cols, device=DEV)].double().cpu().numpy()
+    y_ref = a_rows @ xb
+    z_ref = a_cols.T @ wb
+    assert np.abs(f64(y)[rows] - y_ref).max() <= 2e-5 * np.abs(y_ref).max()
+    assert np.abs(f64(z)[cols] - z_ref).max() <= 5e-5 * np.abs(z_ref).max()
+
+
+def test_fullsize_block_krylov_identities(krylov_workload):
+    import bench
+    a, omega = krylov_workload
+    k, p, v = bench.K_RANK, bench.P_OVER, bench.VIEWS
+    u, s, vv = api().block_krylov(a, k, p, v, omega)
+    assert_status_ok()
+    U, sv, V = f64(u), f64(s), f64(vv)
+    assert np.abs(U.T @ U - np.eye(k)).max() < 1e-5
+    assert np.abs(V.T @ V - np.eye(k)).max() < 1e-5
+    assert np.all(np.diff(sv) <= 0)
+    # A^T U = V diag(s) on 64 sampled columns of A.  Exact for Alg. 9 with v
+    # even, up to the last view's operand: one BF16 term (as timed, Q_c
+    # rounded to 8 bits) or two (split_last, ~16 bits).
+    rng = np.random.default_rng(7)
+    cols = rng.choice(a.shape[1], 64, replace=False)
+    a_cols = a[:, torch.tensor(cols, device=DEV)].double().cpu().numpy()
+
+    def residual(U_, s_, V_):
+        lhs = a_cols.T @ U_
+        rhs = V_[cols] * s_[None, :]
+        return np.linalg.norm(lhs - rhs) / np.linalg.norm(rhs)
+
+    assert residual(U, sv, V) <= 5e-3
+    u2, s2, v2 = api().block_krylov(a, k, p, v, omega, split_last=True)
+    assert_status_ok()
+    assert residual(f64(u2), f64(s2), f64(v2)) <= 2e-4
+    # known spectrum: sigma_j = j^-1.5 up to A's BF16 rounding (|dA| <= 2^-8 |A|)
+    j = np.arange(1, k + 1, dtype=np.float64)
+    assert np.abs(sv[:20] - j[:20] ** -1.5).max() < 5e-3
+
+
+def test_fullsize_single_pass_matches_oracle():
+    cfg = S.CONFIGS["single_pass_20000x10000"]
+    m, n, k = cfg["m"], cfg["n"], cfg["k"]
+    sig = S.sigma_config("exp25", cfg["rank"])
+    a64 = S.usv(m, n, sig, cfg["seed_u"], cfg["seed_v"]) + cfg["noise"] * S.gaussian(m, n, seed=cfg["seed_noise"])
+    a32 = a64.astype(np.float32)
+    del a64
+    om = S.gaussian(n, cfg["ell1"], seed=cfg["seed_omega"]).astype(np.float32)
+    ps = S.gaussian(m, cfg["ell2"], seed=cfg["seed_psi"]).astype(np.float32)
+    t = lambda x: torch.tensor(x, device=DEV)  # noqa: E731
+    u, s, vv = api().single_pass(t(a32), k, t(om), t(ps))
+    assert_status_ok()
+    a = a32.astype(np.float64)
+    uo, so, vo = Al.single_pass(a, om.astype(np.float64), ps.astype(np.float64), k)
+    U, sv, V = f64(u), f64(s), f64(vv)
+    assert np.abs(sv - so).max() / so[0] <= 1e-5
+    e_g = Al.frob_error(a, U, sv, V)
+    e_o = Al.frob_error(a, uo, so, vo)
+    assert abs(e_g - e_o) / e_o <= 1e-5
+    assert np.abs(U.T @ U - np.eye(k)).max() <= 1e-5
+    assert np.abs(V.T @ V - np.eye(k)).max() <= 1e-5

@@ -225,6 +225,30 @@ def test_bf16_form_matches_oracle_on_bf16_matrix(algo):
     assert np.abs(f64(s) - so).max() / so[0] < 1e-3
 
 
+@pytest.mark.parametrize("algo", ["subspace", "krylov"])
+def test_bf16_split_last_view_tightens_singular_values(algo):
+    """split_last: the final view's operand as two BF16 terms.  The last view
+    fixes R (the core), so its products at ~16 operand bits bring the
+    singular values much closer to the FP64 oracle than one BF16 term, while
+    the reconstruction error stays within 1% of it."""
+    m, n, k, p, v = 4096, 2048, 20, 10, 4
+    a64 = S.usv(m, n, S.sigma_config("pow15", n), 31, 32)
+    ab = torch.tensor(a64, dtype=torch.float32).bfloat16()
+    a_exact = ab.double().numpy()
+    om = S.gaussian(n, k + p, seed=33).astype(np.float32)
+    fn = api().subspace_iter if algo == "subspace" else api().block_krylov
+    ref = Al.gen_subspace_iteration if algo == "subspace" else Al.block_krylov
+    uo, so, vo = ref(a_exact, om.astype(np.float64), k, v)
+    u1, s1, v1 = fn(ab.to(DEV), k, p, v, t32(om))
+    u2, s2, v2 = fn(ab.to(DEV), k, p, v, t32(om), split_last=True)
+    assert_status_ok()
+    err1 = np.abs(f64(s1) - so).max() / so[0]
+    err2 = np.abs(f64(s2) - so).max() / so[0]
+    assert err2 < 1e-4 and err2 < 0.1 * err1, (err1, err2)
+    e_o = Al.frob_error(a_exact, uo, so, vo)
+    assert Al.frob_error(a_exact, f64(u2), f64(s2), f64(v2)) <= 1.01 * e_o
+
+
 @pytest.mark.parametrize("algo,m,n,k,p,v", [
     ("subspace", 2048, 1024, 150, 50, 3),    # core 200 x 200: cluster of 2 CTAs
     ("krylov", 4096, 2048, 100, 20, 4),      # core 240 x 240: cluster of 4 CTAs
