@@ -123,9 +123,12 @@ lr_status lr_sketch_chained(lr_handle handle, const lr_mat* A, const lr_mat* X, 
  * Y = Q R, Q^T Q = I, R upper triangular with positive diagonal (the qr of
  * Section 2).  Computed by block CholeskyQR2: column blocks of width <= 128,
  * each projected out of the previous ones twice (BCGS2) and factorised by
- * CholeskyQR2 with FP64-accumulated Grams.  R (ell x ell, F64 column-major)
- * may be NULL.  Rank-deficient Y raises LR_ERR_BREAKDOWN in the status word
- * unless opts->shifted_fallback is set. */
+ * CholeskyQR2 with FP64-accumulated Grams.  When a block's first Cholesky
+ * breaks down (Y ill-conditioned in FP32), that pass is redone with the
+ * shifted Gram of shifted CholeskyQR and a third pass follows (shifted
+ * CholeskyQR3); LR_ERR_BREAKDOWN enters the status word only if even the
+ * shifted factorisation fails (Y numerically rank-deficient).  R (ell x ell,
+ * F64 column-major) may be NULL. */
 lr_status lr_orth(lr_handle handle, lr_mat* Y, lr_mat* R, const lr_opts* opts, void* stream);
 
 /* Generalized subspace iteration, Alg. 2 (Section 4): v >= 2 views, sketch
@@ -159,11 +162,26 @@ lr_status lr_rowwise_single_pass(lr_handle handle, const lr_mat* A, int k, const
 /* Host-streamed single pass (Section 6.1 streaming model, A = sum of column
  * panels): A_host is F32 row-major in pinned host memory; it is copied to the
  * device in panels of panel_cols columns through two device panel buffers
- * (carved from the workspace) on a copy stream overlapped with the sketches.
+ * (carved from the workspace) on a copy stream overlapped with the sketches,
+ * so A crosses the host link once.  The workspace needs
+ * lr_workspace_size(m, n, ell1, ell2, 1) plus 2 * m * round4(panel_cols) * 4
+ * bytes.  Errors: LR_ERR_INVALID_ARG also when A_host is not page-locked.
  * Otherwise as lr_single_pass. */
 lr_status lr_single_pass_host(lr_handle handle, const lr_mat* A_host, int64_t panel_cols, int k,
                               const lr_mat* Omega, const lr_mat* Psi, lr_mat* U, lr_mat* S,
                               lr_mat* V, const lr_opts* opts, void* stream);
+
+/* Alg. 2 (generalized subspace iteration, any v >= 2) on an A kept in pinned
+ * host memory (the out-of-core setting of Section 6.1; every view streams A
+ * once).  A_host: F32 row-major m x n, page-locked (cudaHostAlloc or
+ * cudaHostRegister), never copied whole: each view moves panels of
+ * panel_cols columns through two device buffers on a copy stream while the
+ * previous panel is multiplied.  The workspace needs lr_workspace_size(m, n,
+ * k + p, 0, v) plus 2 * m * round4(panel_cols) * 4 bytes.  Other arguments and
+ * outputs as lr_subspace_iter; errors as lr_single_pass_host. */
+lr_status lr_subspace_iter_host(lr_handle handle, const lr_mat* A_host, int64_t panel_cols, int k, int p, int v,
+                                const lr_mat* Omega, lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts,
+                                void* stream);
 
 /* Reverse pass of lr_subspace_iter for the loss L = sum_i dS_i sigma_i
  * (dS: k weights, F32): writes dA = dL/dA (m x n, F32 row-major, same shape

@@ -17,7 +17,8 @@ from ._binding import (Handle, LowrankError, LrMat, _opts, _stream, col_major, e
 
 __all__ = [
     "sketch", "sketch_chained", "orth", "subspace_iter", "single_pass", "block_krylov",
-    "rowwise_single_pass", "subspace_iter_backward", "single_pass_host", "device_status", "LowrankError",
+    "rowwise_single_pass", "subspace_iter_backward", "single_pass_host", "subspace_iter_host", "device_status",
+    "LowrankError",
 ]
 
 
@@ -194,7 +195,7 @@ def single_pass_host(a_host, k, omega, psi, panel_cols=4096, l_c=None, device=No
     h = Handle.get(dev)
     m, n = a_host.shape
     pc = min(int(panel_cols), n)
-    h.reserve(m, n, omega.shape[1], psi.shape[1], 1, extra=2 * m * pc * 4 + 1024)
+    h.reserve(m, n, omega.shape[1], psi.shape[1], 1, extra=2 * m * ((pc + 3) // 4 * 4) * 4 + 1024)
     u = empty_cm(m, k, dev)
     s = torch.empty(k, dtype=torch.float32, device=dev)
     vv = empty_cm(n, k, dev)
@@ -203,4 +204,29 @@ def single_pass_host(a_host, k, omega, psi, panel_cols=4096, l_c=None, device=No
     o = _opts(l_c=l_c)
     _call(h, lib().lr_single_pass_host, _p(mh), pc, k, _p(mats[0]), _p(mats[1]), _p(mats[2]), _p(mats[3]),
           _p(mats[4]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+def subspace_iter_host(a_host, k, p, v, omega, panel_cols=4096, device=None, stream=None):
+    """Alg. 2 on a pinned host A (float32, row-major): every view streams A in
+    column panels through two device buffers (2 * m * panel_cols floats of
+    workspace) while the previous panel is multiplied."""
+    if a_host.is_cuda or a_host.dtype != torch.float32 or a_host.stride(1) != 1:
+        raise ValueError("a_host must be a row-major float32 CPU tensor")
+    if not a_host.is_pinned():
+        raise ValueError("a_host must be in pinned memory (tensor.pin_memory())")
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    omega = col_major(omega.to(device=dev, dtype=torch.float32))
+    h = Handle.get(dev)
+    m, n = a_host.shape
+    pc = min(int(panel_cols), n)
+    h.reserve(m, n, k + p, 0, v, extra=2 * m * ((pc + 3) // 4 * 4) * 4 + 1024)
+    u = empty_cm(m, k, dev)
+    s = torch.empty(k, dtype=torch.float32, device=dev)
+    vv = empty_cm(n, k, dev)
+    mh = LrMat(a_host.data_ptr(), m, n, a_host.stride(0), 0, 0)
+    mats = [mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts()
+    _call(h, lib().lr_subspace_iter_host, _p(mh), pc, k, p, v, _p(mats[0]), _p(mats[1]), _p(mats[2]),
+          _p(mats[3]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return u, s, vv

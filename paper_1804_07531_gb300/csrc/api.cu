@@ -492,7 +492,14 @@ void write_outputs(Ctx& c, const Mat& Qleft, const float* Lsel, const Mat& Qrigh
 }
 
 // ------------------------------------------------------------ Alg. 2
-void run_subspace(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o) {
+// The views of A a schedule uses: of a device-resident A by default; the
+// host-streamed form supplies its own.
+struct Viewer {
+  std::function<void(Ctx&, const Mat&, Mat)> range;    // Y = A X
+  std::function<void(Ctx&, const Mat&, Mat)> corange;  // Z = A^T W
+};
+
+void run_subspace(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o, const Viewer* vw = nullptr) {
   ArenaScope sc(c.ar);
   Mat Qc{c.ar.take<float>(size_t(A.m) * ell), A.m, ell, A.m};
   Mat Qr{c.ar.take<float>(size_t(A.n) * ell), A.n, ell, A.n};
@@ -504,11 +511,13 @@ void run_subspace(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, O
   Mat cur = Om;  // Q_r = Omega (Alg. 2 starts from the raw Gaussian)
   for (int j = 1; j <= v; ++j) {
     if (j % 2 == 1) {
-      view_range(c, A, cur, Qc, j == v);    // A Q_r
-      orth(c, Qc, Rc);                      // [Q_c, R_c] = qr(A Q_r)
+      if (vw) vw->range(c, cur, Qc);
+      else view_range(c, A, cur, Qc, j == v);    // A Q_r
+      orth(c, Qc, Rc);                           // [Q_c, R_c] = qr(A Q_r)
     } else {
-      view_corange(c, A, Qc, Qr, j == v);   // A^T Q_c
-      orth(c, Qr, Rr);                      // [Q_r, R_r] = qr(A^T Q_c)
+      if (vw) vw->corange(c, Qc, Qr);
+      else view_corange(c, A, Qc, Qr, j == v);   // A^T Q_c
+      orth(c, Qr, Rr);                           // [Q_r, R_r] = qr(A^T Q_c)
       cur = Qr;
     }
   }
@@ -775,16 +784,19 @@ struct HostA {
   int64_t m = 0, n = 0, ld = 0;
 };
 
-void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const Mat& Psi, Mat Y, Mat Z) {
+// Views of a pinned host A streamed in column panels: Y = A X (X: n x ell,
+// when Y is given) and/or Z = A^T W (W: m x ell2, when Z is given), with A
+// crossing the host link once for both.
+void host_views(Ctx& c, const HostA& H, int64_t pc, const Mat* X, Mat* Y, const Mat* W, Mat* Z) {
   ArenaScope sc(c.ar);
   float* buf[2];
   const int64_t ldp = round4(pc);  // panel rows padded to a 16-byte stride (TMA)
   buf[0] = c.ar.take<float>(size_t(H.m) * ldp);
   buf[1] = c.ar.take<float>(size_t(H.m) * ldp);
+  AMat shape;  // an F32 A: the co-range operand is split once for all panels
+  shape.bf16 = false;
   if (c.measure) {
-    AMat shape;
-    shape.bf16 = false;
-    convert_operand(c, shape, nullptr, 0, H.m, int(Psi.cols));
+    if (Z) convert_operand(c, shape, nullptr, 0, H.m, int(W->cols));
     return;
   }
   lr_handle h = c.h;
@@ -795,11 +807,10 @@ void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const
       LR_CHECK_CUDA(cudaEventCreateWithFlags(&h->consumed[i], cudaEventDisableTiming));
     }
   }
-  zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
-  zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
-  AMat shape;  // an F32 A: the co-range operand Psi is split once for all panels
-  shape.bf16 = false;
-  const SplitOp po = convert_operand(c, shape, Psi.p, Psi.ld, H.m, int(Psi.cols));
+  if (Y) zero_f32(Y->p, Y->rows, Y->cols, Y->ld, c.s);
+  if (Z) zero_f32(Z->p, Z->rows, Z->cols, Z->ld, c.s);
+  SplitOp wo;
+  if (Z) wo = convert_operand(c, shape, W->p, W->ld, H.m, int(W->cols));
   // the copy stream starts after everything already queued on the caller's stream
   LR_CHECK_CUDA(cudaEventRecord(h->consumed[0], c.s));
   LR_CHECK_CUDA(cudaStreamWaitEvent(h->copy_stream, h->consumed[0], 0));
@@ -819,12 +830,16 @@ void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const
     P.n = w;
     P.ld = ldp;
     P.bf16 = false;
-    // Y += A_P Omega[c0 : c0 + w, :]
-    view_band(c, P, 0, Om.p + c0, Om.ld, int(Om.cols), Y.p, Y.ld, 0, H.m);
-    // Z[c0 : c0 + w, :] = A_P^T Psi
-    view_band(c, P, 1, Psi.p, Psi.ld, int(Psi.cols), Z.p + c0, Z.ld, 0, H.m, &po);
+    // Y += A_P X[c0 : c0 + w, :]
+    if (Y) view_band(c, P, 0, X->p + c0, X->ld, int(X->cols), Y->p, Y->ld, 0, H.m);
+    // Z[c0 : c0 + w, :] = A_P^T W
+    if (Z) view_band(c, P, 1, W->p, W->ld, int(W->cols), Z->p + c0, Z->ld, 0, H.m, &wo);
     LR_CHECK_CUDA(cudaEventRecord(h->consumed[b], c.s));
   }
+}
+
+void sketch_host_panels(Ctx& c, const HostA& H, int64_t pc, const Mat& Om, const Mat& Psi, Mat Y, Mat Z) {
+  host_views(c, H, pc, &Om, &Y, &Psi, &Z);
 }
 
 // ------------------------------------------------------- validation
@@ -1169,6 +1184,36 @@ lr_status lr_single_pass_host(lr_handle h, const lr_mat* A_host, int64_t panel_c
     const int64_t pc = std::min<int64_t>(panel_cols, a.n);
     run_single_pass(c, a, k, opts ? opts->l_c : -1, om, ps, o,
                     [&](Ctx& cc, Mat Y, Mat Z) { sketch_host_panels(cc, H, pc, om, ps, Y, Z); });
+  });
+}
+
+lr_status lr_subspace_iter_host(lr_handle h, const lr_mat* A_host, int64_t panel_cols, int k, int p, int v,
+                                const lr_mat* Omega, lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts,
+                                void* stream) {
+  return guarded(h, [&] {
+    LR_REQUIRE(A_host && A_host->data, LR_ERR_INVALID_ARG, "A_host is NULL");
+    LR_REQUIRE(A_host->dtype == LR_F32 && A_host->col_major == 0, LR_ERR_DTYPE, "A_host must be F32 row-major");
+    LR_REQUIRE(A_host->rows >= 1 && A_host->cols >= 1 && A_host->ld >= A_host->cols, LR_ERR_SHAPE, "bad A_host");
+    LR_REQUIRE(panel_cols >= 1, LR_ERR_INVALID_ARG, "panel_cols must be positive");
+    cudaPointerAttributes pa{};
+    LR_CHECK_CUDA(cudaPointerGetAttributes(&pa, A_host->data));
+    LR_REQUIRE(pa.type == cudaMemoryTypeHost, LR_ERR_INVALID_ARG, "A_host must be pinned (page-locked) host memory");
+    AMat a;  // shapes only; the data stays on the host
+    a.m = A_host->rows;
+    a.n = A_host->cols;
+    a.ld = A_host->ld;
+    a.bf16 = false;
+    check_kpv(a, k, p, v, 2);
+    const int ell = k + p;
+    Mat om = check_thin(Omega, a.n, ell, "Omega");
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    HostA H{static_cast<const float*>(A_host->data), a.m, a.n, A_host->ld};
+    const int64_t pc = std::min<int64_t>(panel_cols, a.n);
+    Viewer vw;
+    vw.range = [&](Ctx& cc, const Mat& X, Mat Y) { host_views(cc, H, pc, &X, &Y, nullptr, nullptr); };
+    vw.corange = [&](Ctx& cc, const Mat& W, Mat Z) { host_views(cc, H, pc, nullptr, nullptr, &W, &Z); };
+    run_subspace(c, a, k, ell, v, om, o, &vw);
   });
 }
 

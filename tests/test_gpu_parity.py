@@ -286,3 +286,21 @@ def test_host_streamed_single_pass_matches_device_and_oracle(panel):
     assert np.abs(f64(s) - f64(sd)).max() / f64(sd)[0] < 1e-5
     uo, so, vo = Al.single_pass(a32.astype(np.float64), om.astype(np.float64), ps.astype(np.float64), k)
     print(check_tsvd(a32.astype(np.float64), u, s, vv, uo, so, vo))
+
+
+@pytest.mark.parametrize("v,panel", [(2, 700), (3, 1024), (4, 3000)])
+def test_host_streamed_subspace_iteration_matches_device_and_oracle(v, panel):
+    """Alg. 2 with A in pinned host memory, every view streamed in column
+    panels (ragged last panel; one panel when panel >= n): same factorisation
+    as the device-resident form and the oracle."""
+    m, n, k, p = 4096, 3000, 20, 10
+    a64 = S.usv(m, n, S.sigma_config("inv", n), 91, 92) + 1e-5 * S.gaussian(m, n, seed=93)
+    a32 = a64.astype(np.float32)
+    om = S.gaussian(n, k + p, seed=94).astype(np.float32)
+    ah = torch.tensor(a32).pin_memory()
+    u, s, vv = api().subspace_iter_host(ah, k, p, v, torch.tensor(om), panel_cols=panel)
+    assert_status_ok()
+    ud, sd, vd = api().subspace_iter(t32(a32), k, p, v, t32(om))
+    assert np.abs(f64(s) - f64(sd)).max() / f64(sd)[0] < 1e-5
+    uo, so, vo = Al.gen_subspace_iteration(a32.astype(np.float64), om.astype(np.float64), k, v)
+    print(check_tsvd(a32.astype(np.float64), u, s, vv, uo, so, vo))
