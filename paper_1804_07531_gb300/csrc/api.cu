@@ -372,16 +372,22 @@ void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
 // triangular inverse in one CTA).  R (L x L FP64, ld L) receives the
 // triangular factor when non-null: off-diagonal blocks are the summed
 // projection coefficients, diagonal blocks R2 R1.
-void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
+// done: leading columns already orthonormal (the output of an earlier thin
+// QR, as the first block of a Krylov basis is); they are kept as they are
+// and only the remaining columns are projected and factorised (R must then
+// be null).
+void orth(Ctx& c, Mat Y, double* R, int done = 0) {
   const int64_t m = Y.rows;
-  const int L = int(Y.cols);
-  LR_REQUIRE(m >= L, LR_ERR_SHAPE, "orth needs rows >= cols");
+  LR_REQUIRE(m >= Y.cols, LR_ERR_SHAPE, "orth needs rows >= cols");
+  LR_REQUIRE(done == 0 || R == nullptr, LR_ERR_INVALID_ARG, "orth: R is not formed for kept columns");
+  const int L = int(Y.cols) - done;
+  if (L <= 0) return;
   ArenaScope sc(c.ar);
   const int nb = (L + kMaxBlock - 1) / kMaxBlock;
   const int wmax = (L + nb - 1) / nb;
   float* T = c.ar.take<float>(size_t(m) * wmax);
-  double* G64 = c.ar.take<double>(size_t(std::max(L, wmax)) * wmax);
-  float* C32 = c.ar.take<float>(size_t(L) * wmax);
+  double* G64 = c.ar.take<double>(size_t(std::max(L + done, wmax)) * wmax);
+  float* C32 = c.ar.take<float>(size_t(L + done) * wmax);
   float* Rinv = c.ar.take<float>(size_t(wmax) * wmax);
   double* R2 = c.ar.take<double>(size_t(wmax) * wmax);  // factor of a later pass
   int* flags = c.ar.take<int>(size_t(nb));
@@ -389,8 +395,7 @@ void orth(Ctx& c, Mat Y, double* R, bool robust = false) {
   TraceScope tr(c, LR_TRACE_ORTH);
   if (R) LR_CHECK_CUDA(cudaMemsetAsync(R, 0, size_t(L) * L * sizeof(double), c.s));
   LR_CHECK_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * nb, c.s));
-  (void)robust;
-  int c0 = 0;
+  int c0 = done;
   for (int b = 0; b < nb; ++b) {
     const int w = L / nb + (b < L % nb ? 1 : 0);
     float* Yb = Y.col(c0);
@@ -558,7 +563,9 @@ void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Out
     if (in_k) ++blk;
     prev = out;
   }
-  orth(c, K, nullptr, true);             // Q = qr(K)
+  // Q = qr(K); K's first block is already orthonormal (the qr of an inner
+  // view) unless it is the raw last block itself
+  orth(c, K, nullptr, nb >= 2 ? ell : 0);
   if (even) {
     view_corange(c, A, K, F, true);      // A^T Q_c
     orth(c, F, Rf);                      // [Q_r, R_r]
@@ -595,10 +602,10 @@ void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat&
     if (!c.measure) {
       gemm(c, A.n, ell, ell, false, Z.p, Z.ld, false, Ri, ell, blk.p, blk.ld);  // A^T Q_c = Z R_c^{-1}
     }
-    if (i < v - 1) orth(c, blk, nullptr, true);
+    if (i < v - 1) orth(c, blk, nullptr);
     x = blk;
   }
-  orth(c, K, nullptr, true);             // Q_r = qr(K_r)
+  orth(c, K, nullptr, v >= 3 ? ell : 0);  // Q_r = qr(K_r), first block already orthonormal
   view_range(c, A, K, F, true);          // last view: A Q_r
   orth(c, F, Rf);
   core_svd(c, Rf, Lk, W, Vj, Sv);        // R_c = U^ L V^T
