@@ -70,9 +70,15 @@ typedef struct {
   int32_t col_major; /* 1 column-major, 0 row-major */
 } lr_mat;
 
+/* lr_opts.l_c value: choose l_c by the minimum-variance rule of Section 6.5. */
+#define LR_LC_MINVAR (-2)
+
 /* Options; zero-initialise for defaults. */
 typedef struct {
-  int32_t l_c;              /* Alg. 7 truncation oversampling; < 0 means l_c = l_1 */
+  int32_t l_c;              /* Alg. 7 truncation oversampling: 0 <= l_c <= l_1; -1 (or any other
+                               negative value but LR_LC_MINVAR) means l_c = l_1 (the baseline);
+                               LR_LC_MINVAR picks l_c from the sketches (the call then
+                               synchronises its stream once, as the choice sizes the rest) */
   int32_t enhanced;         /* lr_block_krylov: 1 = row-streamed variant of Section 7.3 */
   int32_t split_last;       /* BF16 form: last view's operand as BF16 hi + lo (two products) */
   int32_t shifted_fallback; /* kept for compatibility: every thin QR already retries a

@@ -22,6 +22,8 @@ __all__ = [
     "subspace_iteration", "gen_subspace_iteration", "single_pass", "block_krylov",
     "rowwise_qb_svd", "rowwise_block_krylov", "rel_frob_error", "rel_spec_error",
     "frob_error", "thm31_bound", "thm41_bound", "view_count_block_krylov",
+    "oversampling_flat", "oversampling_decay", "oversampling_rapid", "lc_fixed_ratio",
+    "minvar_spectra", "minvar_lc", "single_pass_minvar",
 ]
 
 
@@ -273,3 +275,76 @@ def thm41_bound(lam, p, l, q):
     t1 = (1.0 + math.sqrt(p / (l - 1.0))) * lam[p] ** e
     t2 = math.e * math.sqrt(p + l) / l * math.sqrt(np.sum(lam[p:] ** (2 * e)))
     return (t1 + t2) ** (1.0 / e)
+
+
+# ------------------------------------------------- Section 6.5 parameters
+def oversampling_flat(T, p):
+    """(l_1, l_2) for a flat spectrum: l_1 = max{2, floor((T - 1) (sqrt(p (T - p - 2)
+    (1 - 2 / (T - 1))) - (p - 1)) / (T - 2p - 1)) - p}, l_2 = T - 2p - l_1."""
+    q = (T - 1) * (math.sqrt(p * (T - p - 2) * (1 - 2 / (T - 1))) - (p - 1)) / (T - 2 * p - 1)
+    l1 = max(2, int(math.floor(q)) - p)
+    return l1, T - 2 * p - l1
+
+
+def oversampling_decay(T, p):
+    """(l_1, l_2) for a moderately decaying spectrum: l_1 = max{2, floor((T - 1) / 3) - p}."""
+    l1 = max(2, int(math.floor((T - 1) / 3)) - p)
+    return l1, T - 2 * p - l1
+
+
+def oversampling_rapid(T, p):
+    """(l_1, l_2) for a rapidly decaying spectrum: l_1 = floor((T - 2) / 2) - p."""
+    l1 = int(math.floor((T - 2) / 2)) - p
+    return l1, T - 2 * p - l1
+
+
+def lc_fixed_ratio(l1, alpha):
+    """l_c = floor(alpha l_1)."""
+    return int(math.floor(alpha * l1))
+
+
+def minvar_spectra(a, omega, psi, k):
+    """Leading k singular values of X(l_c) for l_c = 0 .. l_1 (rows of the result).
+
+    Alg. 7 with each trial l_c: Q_c holds the leading k + l_c left singular
+    vectors of Y_c = A Omega, [Q^, R^] = qr(Psi^T Q_c), X = R^{-1} Q^T Y_r^T
+    with Y_r = A^T Psi.
+    """
+    a = np.asarray(a, dtype=np.float64)
+    yc = a @ omega
+    yr = a.T @ psi
+    ell1 = omega.shape[1]
+    q, r = householder_qr(yc)
+    w, _, _ = jacobi_svd(r)
+    qfull = q @ w                      # left singular vectors of Y_c
+    out = []
+    for lc in range(0, ell1 - k + 1):
+        qc = qfull[:, :k + lc]
+        qh, rh = householder_qr(psi.T @ qc)
+        x = solve_upper(rh, qh.T @ yr.T)
+        _, s, _ = tsvd(x, k)
+        out.append(s)
+    return np.array(out)
+
+
+def minvar_lc(spectra):
+    """The minimum-variance l_c (Section 6.5) from the trial spectra lam[l_c, i]:
+    s(l_c) = [lam(l_c - 1) / lam(l_c), lam(l_c) / lam(l_c), lam(l_c + 1) / lam(l_c)]
+    (the first block absent for l_c = 0), argmin over 0 <= l_c < l_1 of the
+    variance of s(l_c) (population variance; ties go to the smaller l_c)."""
+    lam = np.asarray(spectra, dtype=np.float64)
+    l1 = lam.shape[0] - 1
+    best, arg = np.inf, 0
+    for lc in range(0, l1):
+        parts = [] if lc == 0 else [lam[lc - 1] / lam[lc]]
+        parts += [lam[lc] / lam[lc], lam[lc + 1] / lam[lc]]
+        v = float(np.var(np.concatenate(parts)))
+        if v < best:
+            best, arg = v, lc
+    return arg
+
+
+def single_pass_minvar(a, omega, psi, k):
+    """Alg. 7 with l_c chosen by the minimum-variance rule; returns (out, l_c)."""
+    lc = minvar_lc(minvar_spectra(a, omega, psi, k))
+    return single_pass(a, omega, psi, k, l_c=lc), lc

@@ -204,7 +204,7 @@ def _stream(stream=None) -> int:
 def _opts(l_c=-1, enhanced=False, split_last=False, shifted_fallback=False, band_mb=0) -> LrOpts:
     o = LrOpts()
     o.band_mb = int(band_mb)
-    o.l_c = -1 if l_c is None else int(l_c)
+    o.l_c = -1 if l_c is None else -2 if l_c == "minvar" else int(l_c)
     o.enhanced = int(bool(enhanced))
     o.split_last = int(bool(split_last))
     o.shifted_fallback = int(bool(shifted_fallback))

@@ -144,7 +144,10 @@ def rowwise_single_pass(a, k, omega, stream=None):
 
 
 def single_pass(a, k, omega, psi, l_c=None, stream=None):
-    """Alg. 7: 1-view TSVD (l_c=None: the baseline with l_c = l_1)."""
+    """Alg. 7: 1-view TSVD.  l_c=None: the baseline (l_c = l_1); an int
+    0 <= l_c <= l_1 (e.g. oversampling.fixed_ratio(l_1, 0.5)); "minvar": the
+    minimum-variance rule of Section 6.5, chosen on the device from the
+    sketches (the call synchronises the stream once)."""
     a, (omega, psi) = _prep(a, omega, psi)
     h = Handle.get(a.device)
     m, n = a.shape

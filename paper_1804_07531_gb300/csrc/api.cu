@@ -639,15 +639,84 @@ void run_rowwise_qb(Ctx& c, const AMat& A, int k, int ell, const Mat& Om, Outs& 
 // host-streamed form from column panels copied in from pinned host memory.
 using Sketcher = std::function<void(Ctx&, Mat, Mat)>;
 
+// The minimum-variance l_c of Section 6.5 from the sketches Y = A Omega
+// (m x ell1) and Z = A^T Psi (n x ell2), left intact.  For every trial
+// l_c = 0 .. l1 the leading k singular values of X(l_c) = R^^{-1} Q^^T Z^T
+// are found, where Q^ R^ = qr(Psi^T Q_c[:, :k + l_c]) and Q_c holds the left
+// singular vectors of Y.  Since Z = Q_z R_z, X(l_c) Q_z = R^^{-1} Q^^T R_z^T
+// has the same singular values, so each trial works on small matrices only:
+// X^T = R_z Q^ R^^{-T} (ell2 x (k + l_c)).  A small kernel then picks the
+// l_c whose locally normalised spectra vary least; the choice sizes the rest
+// of Alg. 7, so it is read back (one stream synchronisation).
+int minvar_lc(Ctx& c, const AMat& A, int k, const Mat& Y, const Mat& Z, const Mat& Psi) {
+  ArenaScope sc(c.ar);
+  const int ell1 = int(Y.cols), ell2 = int(Z.cols), l1 = ell1 - k;
+  Mat Yc{c.ar.take<float>(size_t(A.m) * ell1), A.m, ell1, A.m};
+  Mat Zc{c.ar.take<float>(size_t(A.n) * ell2), A.n, ell2, A.n};
+  double* Rc = c.ar.take<double>(size_t(ell1) * ell1);
+  double* Rz = c.ar.take<double>(size_t(ell2) * ell2);
+  float* Wc = c.ar.take<float>(size_t(ell1) * ell1);
+  float* Vc = c.ar.take<float>(size_t(ell1) * ell1);
+  float* Sc = c.ar.take<float>(size_t(ell1));
+  Mat Qf{c.ar.take<float>(size_t(A.m) * ell1), A.m, ell1, A.m};
+  double* B64 = c.ar.take<double>(size_t(ell2) * ell1);
+  float* B = c.ar.take<float>(size_t(ell2) * ell1);
+  float* Rz32 = c.ar.take<float>(size_t(ell2) * ell2);
+  float* Bl = c.ar.take<float>(size_t(ell2) * ell1);
+  double* Rl = c.ar.take<double>(size_t(ell1) * ell1);
+  float* Ri = c.ar.take<float>(size_t(ell1) * ell1);
+  float* M1 = c.ar.take<float>(size_t(ell2) * ell1);
+  float* Xt = c.ar.take<float>(size_t(ell2) * ell1);
+  float* Uj = c.ar.take<float>(size_t(ell2) * ell1);
+  float* Vj = c.ar.take<float>(size_t(ell1) * ell1);
+  float* Sj = c.ar.take<float>(size_t(ell1));
+  float* sig = c.ar.take<float>(size_t(l1 + 1) * k);
+  int* sel = c.ar.take<int>(1);
+  if (c.measure) {  // account for the helpers' own temporaries
+    orth(c, Mat{nullptr, A.m, ell1, A.m}, nullptr);
+    orth(c, Mat{nullptr, A.n, ell2, A.n}, nullptr);
+    orth(c, Mat{nullptr, ell2, ell1, ell2}, nullptr);
+    core_svd(c, nullptr, ell1, nullptr, nullptr, nullptr);
+    tri_inv_any(c, nullptr, ell1, nullptr);
+    return l1;
+  }
+  copy_f32(Y.p, Y.ld, Yc.p, Yc.ld, A.m, ell1, c.s);
+  copy_f32(Z.p, Z.ld, Zc.p, Zc.ld, A.n, ell2, c.s);
+  orth(c, Yc, Rc);                                   // Y = Q R
+  core_svd(c, Rc, ell1, Wc, Vc, Sc);                 // R = W S V^T
+  gemm(c, A.m, ell1, ell1, false, Yc.p, Yc.ld, false, Wc, ell1, Qf.p, Qf.ld);  // left singular vectors of Y
+  gram64(c, ell2, ell1, A.m, Psi.p, Psi.ld, Qf.p, Qf.ld, B64, ell2);          // Psi^T Q_c (all l_c at once)
+  f64_to_f32(B64, ell2, B, ell2, ell2, ell1, c.s);
+  orth(c, Zc, Rz);                                   // Z = Q_z R_z
+  r_to_f32(Rz, ell2, ell2, Rz32, ell2, false, c.s);
+  for (int lc = 0; lc <= l1; ++lc) {
+    const int L = k + lc;
+    copy_f32(B, ell2, Bl, ell2, ell2, L, c.s);
+    orth(c, Mat{Bl, ell2, L, ell2}, Rl);             // [Q^, R^] = qr(Psi^T Q_c)
+    tri_inv_any(c, Rl, L, Ri);
+    gemm(c, ell2, L, ell2, false, Rz32, ell2, false, Bl, ell2, M1, ell2);   // R_z Q^
+    gemm(c, ell2, L, L, false, M1, ell2, true, Ri, L, Xt, ell2);           // X^T = R_z Q^ R^^{-T}
+    jacobi_svd(Xt, ell2, ell2, L, Uj, ell2, Vj, L, Sj, nullptr, c.status, c.s);
+    LR_CHECK_CUDA(cudaMemcpyAsync(sig + size_t(lc) * k, Sj, sizeof(float) * k, cudaMemcpyDeviceToDevice, c.s));
+  }
+  minvar_select(sig, l1 + 1, k, sel, c.s);
+  int h_sel = l1;
+  LR_CHECK_CUDA(cudaMemcpyAsync(&h_sel, sel, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  LR_CHECK_CUDA(cudaStreamSynchronize(c.s));
+  return (h_sel >= 0 && h_sel <= l1) ? h_sel : l1;
+}
+
 void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const Mat& Psi, Outs& o,
                      const Sketcher& sketch = nullptr) {
   ArenaScope sc(c.ar);
   const int ell1 = int(Om.cols), ell2 = int(Psi.cols);
   const int l1 = ell1 - k;
-  const int lc = (l_c < 0 || l_c > l1) ? l1 : l_c;
-  const int Lc = k + lc;
   Mat Y{c.ar.take<float>(size_t(A.m) * ell1), A.m, ell1, A.m};
   Mat Z{c.ar.take<float>(size_t(A.n) * ell2), A.n, ell2, A.n};
+  if (sketch) sketch(c, Y, Z);            // a) Y_c = A Omega_r, b) Y_r = A^T Omega_c
+  else view_dual(c, A, Om, Y, Psi, Z);
+  const int lc = (l_c == LR_LC_MINVAR) ? minvar_lc(c, A, k, Y, Z, Psi) : (l_c < 0 || l_c > l1) ? l1 : l_c;
+  const int Lc = k + lc;
   double* Rc = c.ar.take<double>(size_t(ell1) * ell1);
   Mat Q2{lc < l1 ? c.ar.take<float>(size_t(A.m) * Lc) : nullptr, A.m, Lc, A.m};
   float* Wc = c.ar.take<float>(size_t(ell1) * ell1);
@@ -664,8 +733,6 @@ void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const
   float* Vj = c.ar.take<float>(size_t(Lc) * Lc);
   float* Sv = c.ar.take<float>(size_t(Lc));
 
-  if (sketch) sketch(c, Y, Z);            // a) Y_c = A Omega_r, b) Y_r = A^T Omega_c
-  else view_dual(c, A, Om, Y, Psi, Z);
   orth(c, Y, Rc);                        // [Q_c, R_c] = qr(Y_c)
   Mat Qc = Y;
   if (lc < l1) {

@@ -330,7 +330,45 @@ __global__ void upper_product_kernel(const double* __restrict__ R2, int ld2, dou
   }
 }
 
+// The minimum-variance choice of Section 6.5 from the trial spectra
+// lam[l_c * k + i] (l_c = 0 .. nl - 1): for 0 <= l_c < nl - 1 the vector
+// s(l_c) = [lam(l_c - 1) / lam(l_c), 1, lam(l_c + 1) / lam(l_c)] (the first
+// block absent for l_c = 0); *sel = argmin of its population variance
+// (ties: the smaller l_c).  One thread per trial, then a serial argmin.
+__global__ void minvar_select_kernel(const float* lam, int nl, int k, int* sel) {
+  extern __shared__ double var[];
+  for (int lc = threadIdx.x; lc < nl - 1; lc += blockDim.x) {
+    const float* cur = lam + size_t(lc) * k;
+    double sum = 0.0, sq = 0.0;
+    int cnt = 0;
+    for (int blk = (lc == 0 ? 1 : 0); blk < 3; ++blk) {
+      const float* other = lam + size_t(lc + blk - 1) * k;
+      for (int i = 0; i < k; ++i) {
+        const double r = double(other[i]) / double(cur[i]);
+        sum += r;
+        sq += r * r;
+        ++cnt;
+      }
+    }
+    const double mean = sum / cnt;
+    var[lc] = sq / cnt - mean * mean;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    for (int lc = 1; lc < nl - 1; ++lc)
+      if (var[lc] < var[best]) best = lc;
+    *sel = best;
+  }
+}
+
 }  // namespace
+
+void minvar_select(const float* lam, int nl, int k, int* sel, cudaStream_t s) {
+  LR_REQUIRE(nl >= 2 && k >= 1, LR_ERR_INVALID_ARG, "minimum-variance selection needs l_1 >= 1");
+  minvar_select_kernel<<<1, 256, size_t(nl) * sizeof(double), s>>>(lam, nl, k, sel);
+  LR_LAUNCH_CHECK();
+}
 
 void upper_product(const double* R2, int ld2, double* Racc, int ldr, int n, const int* run_if, cudaStream_t s) {
   if (n <= 0) return;
