@@ -312,11 +312,21 @@ def run_ours(args):
     om_dev = torch.empty(om_host.shape, dtype=om_host.dtype, device=dev)
     e2e_steps = max(1, min(args.steps, 5))
 
+    # the results land in pinned host buffers (allocated once, as a caller
+    # streaming many factorisations would); every step waits for its copy
+    outs_host = None
+
     def e2e_step():
+        nonlocal outs_host
         a_dev.copy_(a_host, non_blocking=True)
         om_dev.copy_(om_host, non_blocking=True)
-        uu, ss, vv = api.block_krylov(a_dev, K_RANK, P_OVER, VIEWS, om_dev)
-        return uu.cpu(), ss.cpu(), vv.cpu()
+        res = api.block_krylov(a_dev, K_RANK, P_OVER, VIEWS, om_dev)
+        if outs_host is None:
+            outs_host = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in res]
+        for h, t in zip(outs_host, res):
+            h.copy_(t, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return outs_host
 
     e2e_step()
     torch.cuda.synchronize()
@@ -471,6 +481,67 @@ def run_case(args):
                       "reps": args.case_reps}), flush=True)
 
 
+def run_host_case(args):
+    """Host-streamed views (A in pinned host memory, streamed in 4096-column
+    panels) against the host link's own roof, measured in the same run as a
+    plain pinned copy of A: Alg. 7 (one view, k = 200, ell1 = 400, ell2 = 800)
+    and Alg. 2 with v = 2 and 3 (every view streams A once).  A is a seeded
+    synthetic m x n FP32 matrix (sigma_j = 1/j on a 200-dimensional part plus
+    1e-5 Gaussian noise), built on the device and copied to the host."""
+    import torch
+
+    from paper_1804_07531_gb300 import api, synth
+    synth._preload_torch_linalg()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    m, n, k, ell1, ell2, pc = args.case_m, args.case_n, 200, 400, 800, 4096
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    r = 200
+    u = torch.linalg.qr(torch.randn(m, r, generator=gen, device=dev))[0]
+    v = torch.linalg.qr(torch.randn(n, r, generator=gen, device=dev))[0]
+    sig = 1.0 / torch.arange(1, r + 1, device=dev, dtype=torch.float32)
+    a_host = torch.empty(m, n, dtype=torch.float32).pin_memory()
+    for i0 in range(0, m, 4096):
+        blk = (u[i0:i0 + 4096] * sig) @ v.t()
+        blk += 1e-5 * torch.randn(blk.shape, generator=gen, device=dev)
+        a_host[i0:i0 + 4096].copy_(blk)
+    del u, v
+    torch.cuda.synchronize()
+    a_bytes = a_host.numel() * 4
+    # the link's roof: a plain pinned host-to-device copy of A
+    d = torch.empty_like(a_host, device=dev)
+    d.copy_(a_host, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    d.copy_(a_host, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    link = a_bytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del d
+    torch.cuda.empty_cache()
+    om = torch.randn(n, ell1, generator=gen, device=dev)
+    ps = torch.randn(m, ell2, generator=gen, device=dev)
+    out = {"case": "host_stream", "m": m, "n": n, "a_gib": round(a_bytes / 2 ** 30, 2), "panel_cols": pc,
+           "link_h2d_gbs": round(link, 1)}
+    runs = [("single_pass_v1", 1, lambda: api.single_pass_host(a_host, k, om, ps, panel_cols=pc))]
+    for vv in (2, 3):
+        runs.append((f"subspace_v{vv}", vv,
+                     lambda vv=vv: api.subspace_iter_host(a_host, k, ell1 - k, vv, om, panel_cols=pc)))
+    for name, views, fn in runs:
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        gbs = views * a_bytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 2), "a_gbs": round(gbs, 1), "frac_of_link": round(gbs / link, 3)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -480,14 +551,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", default=None,
                     choices=["view_range", "view_corange", "view_range_f32", "view_corange_f32", "dual_bf16",
-                             "dual_f32", "chained_bf16", "chained_f32", "orth"],
+                             "dual_f32", "chained_bf16", "chained_f32", "orth", "host_stream"],
                     help="time one entry point on a small case (profiling) instead of the workload")
     ap.add_argument("--case-m", type=int, default=16384)
     ap.add_argument("--case-n", type=int, default=16384)
     ap.add_argument("--case-ell", type=int, default=120)
     ap.add_argument("--case-reps", type=int, default=3)
     args = ap.parse_args()
-    if args.kernel_case:
+    if args.kernel_case == "host_stream":
+        run_host_case(args)
+    elif args.kernel_case:
         run_case(args)
     elif args.impl == "reference":
         run_reference(args)

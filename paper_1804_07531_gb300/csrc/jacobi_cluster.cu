@@ -38,6 +38,7 @@
 
 #include <algorithm>
 
+#include "cluster.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -51,51 +52,12 @@ constexpr int kMaxSweeps = 40;
 constexpr uint64_t kTimeoutNs = 2000000000ull;     // bound of every mbarrier wait
 constexpr size_t kSmemLimit = size_t(225) * 1024;  // dynamic shared memory per CTA
 
-// Pair pi of round rnd (0 <= rnd < np - 1) in the circle method over np
-// positions: position 0 is fixed, the others rotate by one per round.
-__device__ __forceinline__ void round_pair(int pi, int rnd, int np, int& p, int& q) {
-  int ia = pi - 1 + rnd;
-  if (ia >= np - 1) ia -= np - 1;
-  int ib = np - 2 - pi + rnd;
-  if (ib >= np - 1) ib -= np - 1;
-  const int a = (pi == 0) ? 0 : 1 + ia, b = 1 + ib;
-  p = min(a, b);
-  q = max(a, b);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ uint32_t mapa(uint32_t addr, int rank) {
-  uint32_t d;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(addr), "r"(rank));
-  return d;
-}
 // 16-byte store into a peer's shared memory that completes 16 transaction
 // bytes on the peer's mbarrier.
 __device__ __forceinline__ void st_async_v4(uint32_t dst, float a, float b, float c, float d, uint32_t mbar) {
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(dst),
                "f"(a), "f"(b), "f"(c), "f"(d), "r"(mbar)
                : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void cluster_barrier() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // [x y] <- [x y] [[c, s], [-s, c]] on the lane's float4 rows.

@@ -116,12 +116,19 @@ void add_block_f64(double* R, int ldr, int r0, int c0, const double* C, int ldc,
 void f64_to_f32(const double* src, int lds, float* dst, int ldd, int rows, int cols, cudaStream_t s);
 // One-sided Jacobi SVD of M (rows x cols, FP32 col-major, rows >= cols):
 //   M = U diag(S) V^T; U overwrites Wk (rows x cols), V (cols x cols), S desc.
-void jacobi_svd(const float* M, int ldm, int rows, int cols, float* Wk, int ldw, float* V, int ldv, float* S,
+// M is scratch: its contents are destroyed.
+void jacobi_svd(float* M, int ldm, int rows, int cols, float* Wk, int ldw, float* V, int ldv, float* S,
                 double* S64, int* status, cudaStream_t s);
 // Cluster variant for square n x n (rows of W and V split over the P CTAs of
 // a cluster, G lanes per column pair; 0 = the defaults); size 0 when n does
 // not fit.
 int jacobi_cluster_size(int n);
+// Column-block cluster Jacobi (jacobi_block.cu): cluster size for an n x n
+// core (0 if it does not fit), and the SVD itself (P = 0: that size).
+int jacobi_block_size(int n);
+// M (n x n, ld ldm) is read, then overwritten: it holds V while the kernel runs.
+void jacobi_svd_block(float* M, int ldm, int n, float* U, int ldu, float* V, int ldv, float* S, int* status,
+                      cudaStream_t s, int P = 0);
 void jacobi_svd_cluster(const float* M, int ldm, int n, float* U, int ldu, float* V, int ldv, float* S, int* status,
                         cudaStream_t s, int P = 0, int G = 0);
 // Copy a square FP64 upper-triangular R into FP32 (transposed if trans).

@@ -437,14 +437,19 @@ void scale_cols_f32(float* A, int64_t lda, int64_t rows, int cols, const float* 
   LR_LAUNCH_CHECK();
 }
 
-void jacobi_svd(const float* M, int ldm, int rows, int cols, float* Wk, int ldw, float* V, int ldv, float* S,
+void jacobi_svd(float* M, int ldm, int rows, int cols, float* Wk, int ldw, float* V, int ldv, float* S,
                 double* S64, int* status, cudaStream_t s) {
   LR_REQUIRE(rows >= cols && cols >= 1 && cols <= 1024, LR_ERR_UNSUPPORTED, "jacobi_svd: need rows >= cols, cols <= 1024");
   const size_t need = (size_t(rows) * cols + size_t(cols) * cols) * sizeof(float);
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   const size_t cap = size_t(dev_info(dev).max_smem_optin) - 16 * 1024;
-  // square cores wider than one SM comfortably holds: rows split over a cluster
+  // square cores: column blocks over a cluster (2P - 1 exchanges per sweep);
+  // wider ones: rows split over a cluster
+  if (rows == cols && S64 == nullptr && jacobi_block_size(cols) > 0) {
+    jacobi_svd_block(M, ldm, cols, Wk, ldw, V, ldv, S, status, s);
+    return;
+  }
   if (rows == cols && S64 == nullptr && jacobi_cluster_size(cols) > 0) {
     jacobi_svd_cluster(M, ldm, cols, Wk, ldw, V, ldv, S, status, s);
     return;
