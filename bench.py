@@ -458,6 +458,19 @@ def run_case(args):
 
         def call():
             return api.orth(y)
+    elif case == "block_krylov":
+        # the workload's schedule (Alg. 9, v = 4, k = 100, p = 20: a 240 x 240
+        # core) on an m x n BF16 matrix with the same spectrum law
+        from paper_1804_07531_gb300 import synth
+        u = synth.haar_torch(m, n, 21, device=dev)
+        v = synth.haar_torch(n, n, 22, device=dev)
+        sig = torch.tensor(synth.sigma_config("pow15", n), dtype=torch.float32, device=dev)
+        a = ((u * sig[None, :]) @ v.t()).bfloat16()
+        del u, v
+        om = torch.randn(n, K_RANK + P_OVER, generator=gen, device=dev)
+
+        def call():
+            return api.block_krylov(a, K_RANK, P_OVER, VIEWS, om)
     else:
         raise ValueError(case)
     call()
@@ -551,7 +564,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", default=None,
                     choices=["view_range", "view_corange", "view_range_f32", "view_corange_f32", "dual_bf16",
-                             "dual_f32", "chained_bf16", "chained_f32", "orth", "host_stream"],
+                             "dual_f32", "chained_bf16", "chained_f32", "orth", "block_krylov", "host_stream"],
                     help="time one entry point on a small case (profiling) instead of the workload")
     ap.add_argument("--case-m", type=int, default=16384)
     ap.add_argument("--case-n", type=int, default=16384)

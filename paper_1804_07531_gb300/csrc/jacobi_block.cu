@@ -65,7 +65,10 @@ constexpr int kPPW = 32 / kG;                      // pairs per warp
 constexpr int kMaxB = 32;                          // columns per block: J is at most 64 x 64
 constexpr int kVWarps = 4;                         // warps applying V <- V J
 constexpr int kMaxThreads = 32 * ((kMaxB + kPPW - 1) / kPPW + kVWarps);
-constexpr int kMaxTM = 12;                         // float4 per lane per column: n <= 384
+constexpr int kMaxTM = 16;                         // float4 per lane per column: n <= 512
+// Threads of the TM = 16 form: its rows take most registers, so it runs only
+// with blocks of <= 16 columns (4 + kVWarps warps) and a matching bound.
+constexpr int kThreadsTM16 = 32 * ((16 + kPPW - 1) / kPPW + kVWarps);
 constexpr int kMaxSweeps = 40;
 constexpr uint64_t kTimeoutNs = 2000000000ull;     // bound of every mbarrier wait
 constexpr size_t kSmemLimit = size_t(225) * 1024;  // dynamic shared memory per CTA
@@ -79,7 +82,7 @@ struct BGeo {
     NB = 2 * P;                                  // blocks
     b = (n + NB - 1) / NB;                       // columns per block (the last ones zero)
     const int t4 = (n + 4 * kG - 1) / (4 * kG);  // float4 per lane per column, rounded
-    TM = t4 <= 4 ? 4 : t4 <= 8 ? 8 : 12;         // up to the compiled forms
+    TM = t4 <= 4 ? 4 : t4 <= 8 ? 8 : t4 <= 12 ? 12 : 16;  // up to the compiled forms
     npad = 4 * kG * TM;                          // rows, zero-padded
     ldj = 2 * b <= 32 ? 32 : 64;                 // J: 2b x 2b in a ldj x ldj array
     wwarps = (b + kPPW - 1) / kPPW;
@@ -232,7 +235,7 @@ __device__ __noinline__ void apply_vj(float* __restrict__ Vw, int ldv, int n, in
 }
 
 template <int TM, int LDJ>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
     jacobi_block_kernel(float* __restrict__ Mw, int ldm, int n, float* __restrict__ Uout, int ldu,
                         float* __restrict__ Vout, int ldv, float* __restrict__ S, int* status) {
   cg::cluster_group cl = cg::this_cluster();
@@ -536,12 +539,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 using KernelFn = void (*)(float*, int, int, float*, int, float*, int, float*, int*);
 
 KernelFn kernel_for(const BGeo& g) {
-  if (g.ldj == 32) return g.TM == 4 ? jacobi_block_kernel<4, 32> : g.TM == 8 ? jacobi_block_kernel<8, 32>
-                                                                             : jacobi_block_kernel<12, 32>;
+  if (g.ldj == 32)
+    return g.TM == 4 ? jacobi_block_kernel<4, 32> : g.TM == 8 ? jacobi_block_kernel<8, 32>
+                     : g.TM == 12 ? jacobi_block_kernel<12, 32> : jacobi_block_kernel<16, 32>;
   return g.TM == 4 ? jacobi_block_kernel<4, 64> : g.TM == 8 ? jacobi_block_kernel<8, 64> : jacobi_block_kernel<12, 64>;
 }
 bool fits(const BGeo& g, int n) {
-  return g.b <= kMaxB && n <= 4 * kG * kMaxTM && g.threads <= kMaxThreads && g.bytes <= kSmemLimit;
+  if (n > 4 * kG * kMaxTM || g.b > kMaxB || g.bytes > kSmemLimit) return false;
+  return g.TM == 16 ? (g.ldj == 32 && g.threads <= kThreadsTM16) : g.threads <= kMaxThreads;
 }
 
 cudaLaunchConfig_t config(int n, int P, cudaStream_t s, cudaLaunchAttribute* at) {

@@ -250,12 +250,16 @@ def test_bf16_split_last_view_tightens_singular_values(algo):
 
 
 @pytest.mark.parametrize("algo,m,n,k,p,v", [
-    ("subspace", 2048, 1024, 150, 50, 3),    # core 200 x 200: cluster of 2 CTAs
-    ("krylov", 4096, 2048, 100, 20, 4),      # core 240 x 240: cluster of 4 CTAs
-    ("krylov", 4096, 2048, 120, 60, 4),      # core 360 x 360: cluster of 8 CTAs
+    ("subspace", 2048, 1024, 20, 10, 3),     # core 30 x 30: one CTA, blocks of 15 columns
+    ("subspace", 2048, 1024, 40, 24, 3),     # core 64 x 64: 2 CTAs
+    ("subspace", 2048, 1024, 150, 50, 3),    # core 200 x 200: 8 CTAs, 8 float4 rows per lane
+    ("krylov", 4096, 2048, 100, 20, 4),      # core 240 x 240: 8 CTAs (the workload's core)
+    ("krylov", 4096, 2048, 120, 60, 4),      # core 360 x 360: 16 CTAs, 12 float4 rows per lane
+    ("subspace", 4096, 2048, 300, 100, 2),   # core 400 x 400: 16 CTAs, 16 float4 rows per lane
 ])
 def test_wide_core_svd_parity(algo, m, n, k, p, v):
-    """Core SVDs wider than one SM holds run on a thread-block cluster."""
+    """Core SVDs of every width class run on the column-block cluster kernel
+    (one to sixteen CTAs, each form of its per-lane row count)."""
     a64 = S.usv(m, n, S.sigma_config("pow15", n), 61, 62)
     a32 = a64.astype(np.float32)
     a64 = a32.astype(np.float64)
