@@ -221,6 +221,16 @@ lr_status lr_trace_read(lr_handle handle, int kind, double* total_ms, int64_t* l
 /* Number of CUDA kernels this process has launched through the library. */
 lr_status lr_kernel_launches(lr_handle handle, uint64_t* count);
 
+/* Self-test of the bounded waits (no counterpart in the paper).  The
+ * cluster kernels (the core SVD) wait on mbarrier phases that their peer
+ * CTAs complete, each wait bounded (2 s) so that a lost arrival ends in
+ * LR_ERR_TIMEOUT in the device status word instead of a hung GPU.  This call
+ * runs that same bounded wait in one CTA on a phase that nothing completes,
+ * for timeout_us microseconds (1 .. 1000000), then records LR_ERR_TIMEOUT
+ * and returns: read it with lr_get_status.  The kernel ends by itself and
+ * the context stays usable.  Asynchronous on `stream`. */
+lr_status lr_selftest_bounded_wait(lr_handle handle, int64_t timeout_us, void* stream);
+
 /* ---------------------------------------------------------------------
  * Allocation-free range view (the paper has no counterpart).
  * ------------------------------------------------------------------- */

@@ -166,6 +166,15 @@ def device_status(device=None, stream=None) -> int:
     return h.status(stream)
 
 
+def selftest_bounded_wait(timeout_us=20000, device=None, stream=None) -> int:
+    """Run the cluster kernels' bounded wait on a phase nothing completes
+    (lr_selftest_bounded_wait) and return the device status it leaves
+    (LR_ERR_TIMEOUT = 7 when the bound works)."""
+    h = Handle.get(device if device is not None else torch.cuda.current_device())
+    h.check(lib().lr_selftest_bounded_wait(h.h, int(timeout_us), ctypes.c_void_p(_stream(stream))))
+    return h.status(stream)
+
+
 def subspace_iter_backward(a, k, p, v, omega, ds, stream=None):
     """dA for L = sum_i ds_i sigma_i of Alg. 2 (views recomputed, dA written once)."""
     a, (omega,) = _prep(a, omega)

@@ -1351,4 +1351,12 @@ lr_status lr_kernel_launches(lr_handle h, uint64_t* count) {
   return LR_OK;
 }
 
+lr_status lr_selftest_bounded_wait(lr_handle h, int64_t timeout_us, void* stream) {
+  return guarded(h, [&] {
+    LR_REQUIRE(timeout_us >= 1 && timeout_us <= 1000000, LR_ERR_INVALID_ARG, "timeout_us must be in 1..1000000");
+    LR_CHECK_CUDA(cudaSetDevice(h->device));
+    selftest_bounded_wait(h->status_dev, uint64_t(timeout_us) * 1000u, static_cast<cudaStream_t>(stream));
+  });
+}
+
 }  // extern "C"

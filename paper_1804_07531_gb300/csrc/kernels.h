@@ -126,6 +126,10 @@ int jacobi_cluster_size(int n);
 // Column-block cluster Jacobi (jacobi_block.cu): cluster size for an n x n
 // core (0 if it does not fit), and the SVD itself (P = 0: that size).
 int jacobi_block_size(int n);
+// One CTA waits, through the cluster kernels' bounded-wait routine, on an
+// mbarrier phase that nothing completes; records LR_ERR_TIMEOUT after
+// timeout_ns (selftest.cu).
+void selftest_bounded_wait(int* status, uint64_t timeout_ns, cudaStream_t s);
 // M (n x n, ld ldm) is read, then overwritten: it holds V while the kernel runs.
 void jacobi_svd_block(float* M, int ldm, int n, float* U, int ldu, float* V, int ldv, float* S, int* status,
                       cudaStream_t s, int P = 0);

@@ -341,3 +341,25 @@ def test_single_pass_minvar_matches_oracle_choice():
 
     assert lc_g == lc_o or var(lc_g) <= (1 + 1e-3) * var(lc_o), (lc_g, lc_o)
     print(check_tsvd(a, u, s, vv, uo, so, vo))
+
+
+def test_bounded_wait_times_out_and_reports():
+    """The cluster kernels' bounded mbarrier wait, run on a phase that nothing
+    completes, gives up after its bound, records LR_ERR_TIMEOUT, and leaves
+    the context usable (a factorisation right after it is still correct)."""
+    assert api().device_status(0) == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = api().selftest_bounded_wait(20000)
+    e1.record()
+    torch.cuda.synchronize()
+    assert st == 7  # LR_ERR_TIMEOUT
+    assert e0.elapsed_time(e1) >= 19.0  # the wait lasted its bound
+    assert api().device_status(0) == 0  # the status word was read and cleared
+    m, n, k, p = 1024, 512, 16, 8
+    a64 = S.usv(m, n, S.sigma_config("pow15", n), 91, 92)
+    om = S.gaussian(n, k + p, seed=93).astype(np.float32)
+    u, s, vv = api().subspace_iter(t32(a64.astype(np.float32)), k, p, 2, t32(om))
+    assert_status_ok()
+    uo, so, vo = Al.gen_subspace_iteration(a64.astype(np.float32).astype(np.float64), om.astype(np.float64), k, 2)
+    check_tsvd(a64.astype(np.float32).astype(np.float64), u, s, vv, uo, so, vo)
