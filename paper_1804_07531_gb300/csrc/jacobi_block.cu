@@ -38,10 +38,11 @@
 // by the cluster barriers between block rounds.
 //
 // Convergence and faults are decided by the whole cluster from two counters
-// in rank 0's shared memory: rotations (added at the end of every sweep) and
-// CTAs that gave up on an mbarrier wait (added at the next exchange).  All
-// CTAs read them after the same cluster barrier, so all leave the loop at the
-// same exchange and pass the same barriers afterwards.
+// kept in every CTA's shared memory: rotations (every CTA adds its count to
+// all copies at the end of a sweep) and CTAs that gave up on an mbarrier
+// wait (added to all copies at the next exchange).  Every CTA reads its own
+// copy after the same cluster barrier, so all leave the loop at the same
+// exchange and pass the same barriers afterwards.
 //
 // Rotation: zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| +
 // sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t, applied when
@@ -63,12 +64,15 @@ namespace {
 constexpr int kG = 8;                              // lanes per column pair
 constexpr int kPPW = 32 / kG;                      // pairs per warp
 constexpr int kMaxB = 32;                          // columns per block: J is at most 64 x 64
-constexpr int kVWarps = 4;                         // warps applying V <- V J
-constexpr int kMaxThreads = 32 * ((kMaxB + kPPW - 1) / kPPW + kVWarps);
+// Warps applying V <- V J: 8 where the W side is at most 4 warps and its
+// registers leave room (blocks of <= 16 columns, TM <= 12), else 4.
+constexpr int kVWarpsMax = 8, kVWarpsMin = 4;
+constexpr int kMaxThreads = 32 * ((kMaxB + kPPW - 1) / kPPW + kVWarpsMin);
+static_assert(32 * ((16 + kPPW - 1) / kPPW + kVWarpsMax) <= kMaxThreads, "8 V warps fit the bound");
 constexpr int kMaxTM = 16;                         // float4 per lane per column: n <= 512
 // Threads of the TM = 16 form: its rows take most registers, so it runs only
-// with blocks of <= 16 columns (4 + kVWarps warps) and a matching bound.
-constexpr int kThreadsTM16 = 32 * ((16 + kPPW - 1) / kPPW + kVWarps);
+// with blocks of <= 16 columns (4 + kVWarpsMin warps) and a matching bound.
+constexpr int kThreadsTM16 = 32 * ((16 + kPPW - 1) / kPPW + kVWarpsMin);
 constexpr int kMaxSweeps = 40;
 constexpr uint64_t kTimeoutNs = 2000000000ull;     // bound of every mbarrier wait
 constexpr size_t kSmemLimit = size_t(225) * 1024;  // dynamic shared memory per CTA
@@ -86,7 +90,7 @@ struct BGeo {
     npad = 4 * kG * TM;                          // rows, zero-padded
     ldj = 2 * b <= 32 ? 32 : 64;                 // J: 2b x 2b in a ldj x ldj array
     wwarps = (b + kPPW - 1) / kPPW;
-    threads = 32 * (wwarps + kVWarps);
+    threads = 32 * (wwarps + ((TM == 16 || ldj == 64) ? kVWarpsMin : kVWarpsMax));
     ws = b * npad;
     // [2 buffers][2 slots] blocks of W, J of two block rounds, sigma of
     // every column, |w| and 1/|v| of the local columns
@@ -257,8 +261,8 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
   float* wn = sig + npad;           // |w| of the local columns
   float* vi = wn + 64;              // 1/|v| of the local columns
   __shared__ __align__(8) uint64_t full;  // the blocks of the next round landed
-  __shared__ unsigned rot_total;          // rank 0's: rotations so far, all CTAs
-  __shared__ unsigned abort_total;        // rank 0's: CTAs that timed out
+  __shared__ unsigned rot_total;          // rotations so far, all CTAs
+  __shared__ unsigned abort_total;        // CTAs that timed out
   __shared__ int timed_out;
   auto slot = [&](int buf, int s) { return sm + size_t(buf * 2 + s) * ws; };
   auto col4 = [&](int buf, int c) {  // local column c in [0, 2b) of buffer buf
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
 
   const float tol = 1.2e-7f * sqrtf(float(n));
   const float tol2 = tol * tol;
-  const uint32_t rot0 = mapa(smem_u32(&rot_total), 0), abort0 = mapa(smem_u32(&abort_total), 0);
+  const uint32_t rot_l = smem_u32(&rot_total), abort_l = smem_u32(&abort_total);
   int cur = 0, rpos = 0, jb = 0;  // W buffer, block round it is placed for, J buffer
   bool pend = false;              // J of the previous block round waits for V
   int pk0 = 0, pk1 = 0;           // its blocks
@@ -420,14 +424,14 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (sweep_end) {
         const unsigned wr = __reduce_add_sync(0xffffffffu, myrot);
-        if (lane == 0 && wr) asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(rot0), "r"(wr) : "memory");
+        if (wr && lane < P) asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(mapa(rot_l, lane)), "r"(wr) : "memory");
       }
+      if (local_abort && tid < P)
+        asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(mapa(abort_l, tid)), "r"(1u) : "memory");
       if (tid == 0) {
         // the previous sends have finished reading the slots peers refill now
         asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        if (local_abort) {
-          asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(abort0), "r"(1u) : "memory");
-        } else {
+        if (!local_abort) {
           uint32_t bytes = 0;
           for (int s = 0; s < 2; ++s) {
             int hc, hs;
@@ -440,15 +444,11 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
       }
       // also orders the V warps' global writes before the next holders' reads
       cluster_barrier();
-      // every warp reads the cluster's counters itself (the same values: no
-      // CTA adds again before this one has arrived at the next barrier)
-      unsigned ab = 0, tot = 0;
-      if (lane == 0) {
-        asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(ab) : "r"(abort0) : "memory");
-        if (sweep_end) asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(tot) : "r"(rot0) : "memory");
-      }
-      ab = __shfl_sync(0xffffffffu, ab, 0);
-      tot = __shfl_sync(0xffffffffu, tot, 0);
+      // every thread reads this CTA's copies of the counters (the same values
+      // in every CTA: no CTA adds again before all have arrived at the next
+      // barrier, and this one arrives only after these reads)
+      const unsigned ab = *static_cast<volatile unsigned*>(&abort_total);
+      const unsigned tot = sweep_end ? *static_cast<volatile unsigned*>(&rot_total) : 0u;
       if (ab) {
         done = true;  // some CTA gave up: all leave here, nothing moves
         break;
