@@ -152,20 +152,50 @@ __device__ __forceinline__ bool block_cholesky(float* A, float* L, float* X, int
 // Off-diagonal blocks of X = L^{-1} (diagonal blocks already in X), using T
 // as scratch: block row i, for all j < i at once,
 //   T_ij = sum_{m=j..i-1} L_im X_mj,  X_ij = -X_ii T_ij.
+// A thread forms four columns of a row (they share the block column, so the
+// same summation range): each L or X entry it loads feeds four products.
 __device__ __forceinline__ void block_inverse_offdiag(const float* L, float* X, float* T, int N, int ld) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nb = N / kB;
   for (int i = 1; i < nb; ++i) {
     const int i0 = i * kB;
-    for (int idx = tid; idx < kB * i0; idx += nt) {
-      const int r = idx % kB, cc = idx / kB;  // row i0 + r, column cc < i0
-      const int m0 = (cc / kB) * kB;
-      T[(i0 + r) + cc * ld] = dot4(L + (i0 + r), ld, X + cc * ld, 1, m0, i0);
+    for (int idx = tid; idx < kB * (i0 / 4); idx += nt) {
+      const int r = idx % kB, c0 = (idx / kB) * 4;  // row i0 + r, columns c0..c0+3 < i0
+      const int m0 = (c0 / kB) * kB;
+      const float* lr = L + (i0 + r);
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int m = m0; m < i0; ++m) {
+        const float l = lr[m * ld];
+        const float* xm = X + m + c0 * ld;
+        a0 = fmaf(l, xm[0], a0);
+        a1 = fmaf(l, xm[ld], a1);
+        a2 = fmaf(l, xm[2 * ld], a2);
+        a3 = fmaf(l, xm[3 * ld], a3);
+      }
+      float* t = T + (i0 + r) + c0 * ld;
+      t[0] = a0;
+      t[ld] = a1;
+      t[2 * ld] = a2;
+      t[3 * ld] = a3;
     }
     __syncthreads();
-    for (int idx = tid; idx < kB * i0; idx += nt) {
-      const int r = idx % kB, cc = idx / kB;
-      X[(i0 + r) + cc * ld] = -dot4(X + (i0 + r) + i0 * ld, ld, T + i0 + cc * ld, 1, 0, r + 1);
+    for (int idx = tid; idx < kB * (i0 / 4); idx += nt) {
+      const int r = idx % kB, c0 = (idx / kB) * 4;
+      const float* xr = X + (i0 + r) + i0 * ld;  // row i0 + r of X_ii
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int m = 0; m <= r; ++m) {
+        const float x = xr[m * ld];
+        const float* tm = T + (i0 + m) + c0 * ld;
+        a0 = fmaf(x, tm[0], a0);
+        a1 = fmaf(x, tm[ld], a1);
+        a2 = fmaf(x, tm[2 * ld], a2);
+        a3 = fmaf(x, tm[3 * ld], a3);
+      }
+      float* xo = X + (i0 + r) + c0 * ld;
+      xo[0] = -a0;
+      xo[ld] = -a1;
+      xo[2 * ld] = -a2;
+      xo[3 * ld] = -a3;
     }
     __syncthreads();
   }
@@ -201,16 +231,16 @@ __global__ void __launch_bounds__(kThreadsC) chol_inv_kernel(const double* __res
     if (tid == 0) tr = t;
   }
   __syncthreads();
-  // loads issued four at a time so that their latencies overlap
-  for (int base = tid; base < N * N; base += 4 * nt) {
-    double g[4];
+  // loads issued eight at a time so that their latencies overlap
+  for (int base = tid; base < N * N; base += 8 * nt) {
+    double g[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int idx = base + u * nt, r = idx % N, c = idx / N;
       g[u] = (idx < N * N && r < n && c < n) ? G[r + c * n] : (r == c ? 1.0 : 0.0);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int idx = base + u * nt, r = idx % N, c = idx / N;
       if (idx >= N * N) continue;
       if (!isfinite(g[u])) nonfinite = 1;
@@ -296,16 +326,16 @@ __global__ void __launch_bounds__(kThreadsC) tri_inv_kernel(const double* __rest
   float* X = L + N * ld;
   float* T = X + N * ld;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid / 32, lane = tid % 32;
-  // loads issued four at a time so that their latencies overlap
-  for (int base = tid; base < N * N; base += 4 * nt) {
-    double g[4];
+  // loads issued eight at a time so that their latencies overlap
+  for (int base = tid; base < N * N; base += 8 * nt) {
+    double g[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int idx = base + u * nt, r = idx % N, c = idx / N;
       g[u] = (idx < N * N && r < n && c < n) ? (r >= c ? R[c + r * ldr] : 0.0) : (r == c ? 1.0 : 0.0);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int idx = base + u * nt, r = idx % N, c = idx / N;
       if (idx >= N * N) continue;
       const float v = float(g[u]);
