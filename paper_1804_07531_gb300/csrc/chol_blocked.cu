@@ -6,11 +6,14 @@
 // The factorisation G = L L^T (L = R^T) runs on 32 x 32 blocks.  For block
 // column k:
 //   A. one warp factors the diagonal block in registers (lane i holds row i;
-//      column j's multipliers are broadcast by shuffles) and inverts its
-//      factor L_kk by forward substitution (lane j computes column j);
+//      column j's multipliers are broadcast through shared memory) and
+//      inverts its factor L_kk by forward substitution (lane j computes
+//      column j);
 //   B. the whole CTA forms the panel L_ik = A_ik L_kk^{-T} for the blocks
 //      below;
 //   C. the whole CTA applies the trailing update A_ij -= L_ik L_jk^T.
+// In B, C and the inverse's off-diagonal blocks a thread forms four entries
+// of one row, so each shared-memory load of that row feeds four products.
 // The off-diagonal blocks of X = L^{-1} then follow block row by block row:
 // X_ij = -X_ii sum_{m=j..i-1} L_im X_mj.  About a dozen CTA barriers replace
 // the one barrier per column (and per row of the inverse) of an unblocked
@@ -132,17 +135,51 @@ __device__ __forceinline__ bool block_cholesky(float* A, float* L, float* X, int
     if (*bad) return true;
     const int k1 = k0 + kB, rows = N - k1;
     if (rows == 0) break;
-    // B. panel L_ik = A_ik X_kk^T (row r of the panel, column c of the block)
-    for (int idx = tid; idx < rows * kB; idx += nt) {
-      const int r = k1 + idx % rows, c = idx / rows;
-      L[r + (k0 + c) * ld] = dot4(A + r + k0 * ld, ld, X + (k0 + c) + k0 * ld, ld, 0, c + 1);
+    // B. panel L_ik = A_ik X_kk^T: row r, columns c0..c0+3 of the block per
+    // thread (X_kk is exactly zero above its diagonal, so the four sums can
+    // share the range m <= c0 + 3)
+    for (int idx = tid; idx < rows * (kB / 4); idx += nt) {
+      const int r = k1 + idx % rows, c0 = (idx / rows) * 4;
+      const float* ar = A + r + k0 * ld;
+      const float* xc = X + (k0 + c0) + k0 * ld;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int m = 0; m <= c0 + 3; ++m) {
+        const float a = ar[m * ld];
+        const float* xm = xc + m * ld;
+        a0 = fmaf(a, xm[0], a0);
+        a1 = fmaf(a, xm[1], a1);
+        a2 = fmaf(a, xm[2], a2);
+        a3 = fmaf(a, xm[3], a3);
+      }
+      float* lo = L + r + (k0 + c0) * ld;
+      lo[0] = a0;
+      lo[ld] = a1;
+      lo[2 * ld] = a2;
+      lo[3 * ld] = a3;
     }
     __syncthreads();
-    // C. trailing update of the lower part: A_ij -= L_ik L_jk^T
-    for (int idx = tid; idx < rows * rows; idx += nt) {
-      const int i = k1 + idx % rows, j = k1 + idx / rows;
-      if (i < j) continue;
-      A[i + j * ld] -= dot4(L + i + k0 * ld, ld, L + j + k0 * ld, ld, 0, kB);
+    // C. trailing update of the lower part: A_ij -= L_ik L_jk^T, row i and
+    // columns j0..j0+3 per thread
+    for (int idx = tid; idx < rows * (rows / 4); idx += nt) {
+      const int i = k1 + idx % rows, j0 = k1 + (idx / rows) * 4;
+      if (i < j0) continue;
+      const float* li = L + i + k0 * ld;
+      const float* lj = L + j0 + k0 * ld;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 8
+      for (int m = 0; m < kB; ++m) {
+        const float l = li[m * ld];
+        const float* lm = lj + m * ld;
+        a0 = fmaf(l, lm[0], a0);
+        a1 = fmaf(l, lm[1], a1);
+        a2 = fmaf(l, lm[2], a2);
+        a3 = fmaf(l, lm[3], a3);
+      }
+      float* ai = A + i + j0 * ld;
+      ai[0] -= a0;
+      if (i >= j0 + 1) ai[ld] -= a1;
+      if (i >= j0 + 2) ai[2 * ld] -= a2;
+      if (i >= j0 + 3) ai[3 * ld] -= a3;
     }
     __syncthreads();
   }
