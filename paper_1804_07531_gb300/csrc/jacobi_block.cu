@@ -45,8 +45,9 @@
 // exchange and pass the same barriers afterwards.
 //
 // Rotation: zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| +
-// sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t, applied when
-// gamma^2 > tol^2 alpha beta (tol = eps sqrt(n)).  t only has to be close (an
+// sqrt(1 + zeta^2)) (computed without forming zeta, see angle()),
+// c = 1 / sqrt(1 + t^2), s = c t, applied when gamma^2 > tol^2 alpha beta
+// (tol = eps sqrt(n)).  t only has to be close (an
 // inexact angle is still a rotation); c is the refined reciprocal square
 // root, so c^2 + s^2 = 1 to about an ulp.  Outputs: sigma_i = |w_i| / |v_i|,
 // u_i = w_i / |w_i|, v_i / |v_i|, sorted by sigma descending (ties by index).

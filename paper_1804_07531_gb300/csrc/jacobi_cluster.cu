@@ -1,10 +1,13 @@
-// One-sided Jacobi SVD of a square core matrix on a thread-block cluster.
+// One-sided Jacobi SVD of a square core matrix on a thread-block cluster,
+// rows split over the CTAs.
 //
 // The core SVD (the final tsvd of R_r or R_c in Alg. 2 and Alg. 9, and of the
-// small factors of Alg. 7) is an n x n problem with n up to a few hundred.
-// One-sided Jacobi on M: W = M V, rotating column pairs of W (and V) until
-// every pair is orthogonal to working precision; then sigma_i = |w_i|,
-// u_i = w_i / sigma_i.
+// small factors of Alg. 7) is an n x n problem.  Cores of n <= 512 run on the
+// column-block kernel (jacobi_block.cu), which exchanges data 2P - 1 times
+// per sweep instead of once per round; this kernel serves the wider square
+// cores whose W and V fit the cluster's shared memory.  One-sided Jacobi on
+// M: W = M V, rotating column pairs of W (and V) until every pair is
+// orthogonal to working precision; then sigma_i = |w_i|, u_i = w_i / sigma_i.
 //
 // The work is latency-bound: a sweep is n - 1 rounds of n / 2 disjoint
 // rotations (circle-method ordering), and every round needs three inner
