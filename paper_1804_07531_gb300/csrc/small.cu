@@ -15,14 +15,6 @@ namespace lr {
 
 namespace {
 
-__global__ void zero_kernel(float* p, int64_t rows, int64_t cols, int64_t ld) {
-  int64_t total = rows * cols;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    int64_t r = i % rows, c = i / rows;
-    p[r + c * ld] = 0.f;
-  }
-}
-
 __global__ void f32_to_bf16_kernel(const float* __restrict__ src, int64_t lds, __nv_bfloat16* __restrict__ dst,
                                    __nv_bfloat16* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols) {
   int64_t total = rows * cols;
@@ -47,15 +39,32 @@ __global__ void copy_kernel(const float* __restrict__ src, int64_t lds, float* _
 
 // One block per column i: find the entry of U(:, i) with the largest
 // magnitude (lowest index on ties) and flip (u_i, v_i) if it is negative.
-__global__ void fix_signs_kernel(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n) {
+// 1024 threads and float4 loads (when the column is 16-byte aligned) keep
+// enough loads in flight for a column of 64k rows.
+__device__ __forceinline__ void take_max(float a, int64_t r, float& best, int64_t& bidx) {
+  if (a > best) {  // rows are visited in increasing order: the first maximum stays
+    best = a;
+    bidx = r;
+  }
+}
+__global__ void __launch_bounds__(1024) fix_signs_kernel(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv,
+                                                         int64_t n) {
   const int col = blockIdx.x;
   float* u = U + col * ldu;
   float best = -1.f;
   int64_t bidx = 0;
-  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
-    float a = fabsf(u[r]);
-    if (a > best) { best = a; bidx = r; }
+  const bool vec = (reinterpret_cast<uintptr_t>(u) & 15) == 0;
+  const int64_t m4 = vec ? m / 4 : 0;
+  const float4* u4 = reinterpret_cast<const float4*>(u);
+#pragma unroll 4
+  for (int64_t q = threadIdx.x; q < m4; q += blockDim.x) {
+    const float4 x = u4[q];
+    take_max(fabsf(x.x), 4 * q, best, bidx);
+    take_max(fabsf(x.y), 4 * q + 1, best, bidx);
+    take_max(fabsf(x.z), 4 * q + 2, best, bidx);
+    take_max(fabsf(x.w), 4 * q + 3, best, bidx);
   }
+  for (int64_t r = 4 * m4 + threadIdx.x; r < m; r += blockDim.x) take_max(fabsf(u[r]), r, best, bidx);
   __shared__ float sb[32];
   __shared__ int64_t si[32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -81,7 +90,12 @@ __global__ void fix_signs_kernel(float* U, int64_t ldu, int64_t m, float* V, int
   const bool flip = u[si[0]] < 0.f;
   __syncthreads();
   if (!flip) return;
-  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) u[r] = -u[r];
+  float4* w4 = reinterpret_cast<float4*>(u);
+  for (int64_t q = threadIdx.x; q < m4; q += blockDim.x) {
+    const float4 x = w4[q];
+    w4[q] = make_float4(-x.x, -x.y, -x.z, -x.w);
+  }
+  for (int64_t r = 4 * m4 + threadIdx.x; r < m; r += blockDim.x) u[r] = -u[r];
   float* v = V + col * ldv;
   for (int64_t r = threadIdx.x; r < n; r += blockDim.x) v[r] = -v[r];
 }
@@ -405,7 +419,7 @@ void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t ro
 
 void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n, int k, cudaStream_t s) {
   if (k <= 0) return;
-  fix_signs_kernel<<<k, 256, 0, s>>>(U, ldu, m, V, ldv, n);
+  fix_signs_kernel<<<k, 1024, 0, s>>>(U, ldu, m, V, ldv, n);
   LR_LAUNCH_CHECK();
 }
 
