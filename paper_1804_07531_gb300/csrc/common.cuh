@@ -88,6 +88,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 inline int ceil_div(int64_t a, int64_t b) { return int((a + b - 1) / b); }
+// Grid (256-thread blocks) for an element-wise pass over a rows x cols
+// column-major matrix: x strides over rows, y over columns, so a thread
+// needs no division to find its element.
+inline dim3 grid_2d(int64_t rows, int64_t cols) {
+  const int64_t gx = (rows + 255) / 256;
+  return dim3(unsigned(gx < 64 ? gx : 64), unsigned(cols < 1024 ? cols : 1024), 1);
+}
 
 // Device properties needed for grid sizing (cached per device).
 struct DevInfo {

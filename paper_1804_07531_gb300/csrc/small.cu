@@ -17,24 +17,22 @@ namespace {
 
 __global__ void f32_to_bf16_kernel(const float* __restrict__ src, int64_t lds, __nv_bfloat16* __restrict__ dst,
                                    __nv_bfloat16* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols) {
-  int64_t total = rows * cols;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    int64_t r = i % rows, c = i / rows;
-    float x = src[r + c * lds];
-    __nv_bfloat16 h = __float2bfloat16_rn(x);
-    dst[r + c * ldd] = h;
-    if (lo) lo[r + c * ldd] = __float2bfloat16_rn(x - __bfloat162float(h));
-  }
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
+      const float x = src[r + c * lds];
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      dst[r + c * ldd] = h;
+      if (lo) lo[r + c * ldd] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
 }
 
 __global__ void copy_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ dst, int64_t ldd,
                             int64_t rows, int64_t cols, const int* run_if) {
   if (run_if && *run_if == 0) return;
-  int64_t total = rows * cols;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    int64_t r = i % rows, c = i / rows;
-    dst[r + c * ldd] = src[r + c * lds];
-  }
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
+      dst[r + c * ldd] = src[r + c * lds];
+    }
 }
 
 // One block per column i: find the entry of U(:, i) with the largest
@@ -125,11 +123,10 @@ __global__ void r_to_f32_kernel(const double* R, int ldr, int n, float* out, int
 }
 
 __global__ void scale_cols_kernel(float* A, int64_t lda, int64_t rows, int cols, const float* scale) {
-  int64_t total = rows * cols;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    int64_t r = i % rows, c = i / rows;
-    A[r + c * lda] *= scale[c];
-  }
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
+      A[r + c * lda] *= scale[c];
+    }
 }
 
 // --------------------------------------------------------- Jacobi SVD
@@ -406,14 +403,14 @@ void zero_bytes(void* p, size_t bytes, cudaStream_t s) {
 void f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, __nv_bfloat16* lo, int64_t ldd, int64_t rows,
                  int64_t cols, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return;
-  f32_to_bf16_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, lo, ldd, rows, cols);
+  f32_to_bf16_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(src, lds, dst, lo, ldd, rows, cols);
   LR_LAUNCH_CHECK();
 }
 
 void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
               const int* run_if) {
   if (rows <= 0 || cols <= 0) return;
-  copy_kernel<<<grid_for(rows * cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols, run_if);
+  copy_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(src, lds, dst, ldd, rows, cols, run_if);
   LR_LAUNCH_CHECK();
 }
 
@@ -447,7 +444,7 @@ void qr_bwd_sym(const float* M, const double* C, int n, float* out, cudaStream_t
 
 void scale_cols_f32(float* A, int64_t lda, int64_t rows, int cols, const float* scale, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return;
-  scale_cols_kernel<<<grid_for(rows * cols), 256, 0, s>>>(A, lda, rows, cols, scale);
+  scale_cols_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(A, lda, rows, cols, scale);
   LR_LAUNCH_CHECK();
 }
 

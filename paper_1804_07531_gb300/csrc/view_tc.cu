@@ -659,14 +659,13 @@ __global__ void __launch_bounds__(kThreadsT, 1)
 
 __global__ void split_tf32_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ hi,
                                   float* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols, float scale) {
-  const int64_t total = rows * cols;
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = i % rows, c = i / rows;
-    const float x = scale * src[r + c * lds];
-    const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-    hi[r + c * ldd] = h;
-    lo[r + c * ldd] = x - h;
-  }
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
+      const float x = scale * src[r + c * lds];
+      const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+      hi[r + c * ldd] = h;
+      lo[r + c * ldd] = x - h;
+    }
 }
 
 // ------------------------------------------------------------------ host
@@ -810,8 +809,7 @@ void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMa
 void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd, int64_t rows, int64_t cols,
                 cudaStream_t s, float scale) {
   if (rows <= 0 || cols <= 0) return;
-  const int grid = int(std::min<int64_t>(4096, (rows * cols + 255) / 256));
-  split_tf32_kernel<<<grid, 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, scale);
+  split_tf32_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, scale);
   LR_LAUNCH_CHECK();
 }
 
