@@ -67,10 +67,10 @@ __device__ __forceinline__ float dot4(const float* a, int sa, const float* b, in
 
 // Factors the symmetric block at (k0, k0) of A (lower part used) as L L^T in
 // registers -- lane i holds row i -- and writes the rows of L_kk (zeros above
-// the diagonal) to L.  Column j of the factor is broadcast through shared
-// memory (col, 32 floats): one store per lane, then independent loads, so
-// the loads of a step overlap instead of serialising like a chain of warp
-// shuffles.  Returns false in every lane on a pivot that is not positive and
+// the diagonal) to L.  The pivot comes from lane j by one shuffle; column j
+// of the factor is broadcast through shared memory (col, 32 floats): one
+// store per lane, then independent loads, so the loads of a step overlap
+// instead of serialising like a chain of warp shuffles.  Returns false in every lane on a pivot that is not positive and
 // finite.
 __device__ __noinline__ bool warp_factor_block(const float* A, float* L, int ld, int k0, int lane, float* col) {
   float a[kB];
@@ -80,9 +80,7 @@ __device__ __noinline__ bool warp_factor_block(const float* A, float* L, int ld,
 #pragma unroll
   for (int j = 0; j < kB; ++j) {
     // the pivot: lane j's updated diagonal entry
-    if (lane == j) col[32] = a[j];
-    __syncwarp();
-    const float d = col[32];
+    const float d = __shfl_sync(0xffffffffu, a[j], j);
     ok = ok && (d > 0.f) && isfinite(d);
     const float dd = fmaxf(d, 1e-30f);
     const float inv = rsqrt_refined(dd);  // 1 / l_jj
