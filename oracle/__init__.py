@@ -13,7 +13,7 @@ Contents
   algorithms  the paper's algorithms step by step in its order: Alg. 1, Alg. 2
               (generalized subspace iteration), Alg. 7 (single pass, Tropp
               variant with l_c), Alg. 9 (generalized block Krylov), the
-              row-streamed one-pass QB of Section 6.7 and the row-streamed
+              row-streamed one-pass QB of Section 6.8 and the row-streamed
               block Krylov method of Section 7.3, plus the error measures of
               Section 8.2 and the bounds of Theorems 3.1 and 4.1.
   grad        reverse-mode derivative of the sum of the top-k estimated

@@ -76,7 +76,7 @@ def gen_subspace_iteration(a, omega, k, v, return_state=False):
 
 
 def single_pass(a, omega, psi, k, l_c=None, return_state=False):
-    """Alg. 7 (Section 6.4): 1-view TSVD, Tropp variant with truncation l_c.
+    """Alg. 7 (Section 6.5): 1-view TSVD, Tropp variant with truncation l_c.
 
     omega: n x (k + l_1), psi: m x (k + l_2), l_2 >= l_1 >= l_c >= 0.
     Y_c = A Omega and Y_r = A^T Psi (one view); if l_c < l_1:
@@ -149,7 +149,7 @@ def block_krylov(a, omega, k, v, return_state=False):
 def _rowwise_pass(a, x, rows_per_block=256):
     """One pass over the rows of A: Y[i,:] = A[i,:] X and Z = sum_i A[i,:]^T Y[i,:].
 
-    This is the row-streamed evaluation of Section 6.7: each block of rows is
+    This is the row-streamed evaluation of Section 6.8: each block of rows is
     used for its slice of Y and, while it is at hand, for its contribution to
     A^T Y.  The result equals (A X, A^T A X).
     """
@@ -164,7 +164,7 @@ def _rowwise_pass(a, x, rows_per_block=256):
 
 
 def rowwise_qb_svd(a, omega, k):
-    """Section 6.7: one row-streamed pass giving the 2-view QB factorisation.
+    """Section 6.8: one row-streamed pass giving the 2-view QB factorisation.
 
     Y_c = A Omega and Y^_r = A^T Y_c from one pass; [Q_c, R_c] = qr(Y_c);
     B solves B^T R_c = Y^_r (B^T = Y^_r R_c^{-1} = A^T Q_c for invertible
@@ -184,7 +184,7 @@ def rowwise_block_krylov(a, omega, k, v, return_state=False):
     """Section 7.3: block Krylov for row-streamed A, v views (v >= 2).
 
     Each of views 1..v-1 is one row-streamed pass giving Y = A X and
-    Z = A^T Y (Section 6.7); with [Q_c, R_c] = qr(Y), A^T Q_c = Z R_c^{-1}
+    Z = A^T Y (Section 6.8); with [Q_c, R_c] = qr(Y), A^T Q_c = Z R_c^{-1}
     is the next co-range block: orthonormalised (X = qr(Z R_c^{-1})) except
     after view v-1, where it is kept raw.  The co-range Krylov space
     K_r = [A^T Q_c^1 .. A^T Q_c^{v-1}] thus holds v-1 blocks from v-1 views
@@ -277,7 +277,7 @@ def thm41_bound(lam, p, l, q):
     return (t1 + t2) ** (1.0 / e)
 
 
-# ------------------------------------------------- Section 6.5 parameters
+# ------------------------------- Section 6.3 (FLAT/DECAY/RAPID) and 6.6 (l_c) parameters
 def oversampling_flat(T, p):
     """(l_1, l_2) for a flat spectrum: l_1 = max{2, floor((T - 1) (sqrt(p (T - p - 2)
     (1 - 2 / (T - 1))) - (p - 1)) / (T - 2p - 1)) - p}, l_2 = T - 2p - l_1."""
@@ -328,7 +328,7 @@ def minvar_spectra(a, omega, psi, k):
 
 
 def minvar_lc(spectra):
-    """The minimum-variance l_c (Section 6.5) from the trial spectra lam[l_c, i]:
+    """The minimum-variance l_c (Section 6.6) from the trial spectra lam[l_c, i]:
     s(l_c) = [lam(l_c - 1) / lam(l_c), lam(l_c) / lam(l_c), lam(l_c + 1) / lam(l_c)]
     (the first block absent for l_c = 0), argmin over 0 <= l_c < l_1 of the
     variance of s(l_c) (population variance; ties go to the smaller l_c)."""

@@ -62,7 +62,7 @@ def sketch(a, x=None, w=None, stream=None, band_mb=0):
 
 
 def sketch_chained(a, x, stream=None, band_mb=0):
-    """Y = A X and Z = A^T Y from one read of A (Section 6.7)."""
+    """Y = A X and Z = A^T Y from one read of A (Section 6.8)."""
     a, (x,) = _prep(a, x)
     h = Handle.get(a.device)
     m, n = a.shape
@@ -130,7 +130,7 @@ def block_krylov(a, k, p, v, omega, enhanced=False, shifted_fallback=False, spli
 
 
 def rowwise_single_pass(a, k, omega, stream=None):
-    """Section 6.7: 2-view-accurate TSVD from one row-streamed read of A."""
+    """Section 6.8: 2-view-accurate TSVD from one row-streamed read of A."""
     a, (omega,) = _prep(a, omega)
     h = Handle.get(a.device)
     m, n = a.shape
@@ -146,7 +146,7 @@ def rowwise_single_pass(a, k, omega, stream=None):
 def single_pass(a, k, omega, psi, l_c=None, stream=None):
     """Alg. 7: 1-view TSVD.  l_c=None: the baseline (l_c = l_1); an int
     0 <= l_c <= l_1 (e.g. oversampling.fixed_ratio(l_1, 0.5)); "minvar": the
-    minimum-variance rule of Section 6.5, chosen on the device from the
+    minimum-variance rule of Section 6.6, chosen on the device from the
     sketches (the call synchronises the stream once)."""
     a, (omega, psi) = _prep(a, omega, psi)
     h = Handle.get(a.device)

@@ -4,7 +4,7 @@
 //   lr_single_pass          Alg. 7 (1-view, Tropp variant with l_c)
 //   lr_block_krylov         Alg. 9 (generalized block Krylov) and, with
 //                           opts->enhanced, the row-streamed variant of Sec. 7.3
-//   lr_rowwise_single_pass  the one-pass QB of Section 6.7
+//   lr_rowwise_single_pass  the one-pass QB of Section 6.8
 // plus the building blocks lr_sketch / lr_sketch_chained (views) and lr_orth
 // (thin QR by block CholeskyQR2).  Every step runs in this library's kernels.
 #include <algorithm>
@@ -335,7 +335,7 @@ void view_dual(Ctx& c, const AMat& A, const Mat& X, Mat Y, const Mat& W, Mat Z) 
   }
 }
 
-// Y = A X and Z = A^T Y (Section 6.7): each band of rows gives its slice of
+// Y = A X and Z = A^T Y (Section 6.8): each band of rows gives its slice of
 // Y, which is converted and used for that band's share of A^T Y.
 void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
   ArenaScope sc(c.ar);
@@ -612,7 +612,7 @@ void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat&
   write_outputs(c, F, W, K, Vj, Lk, Sv, k, o);
 }
 
-// ------------------------------------------------------- Section 6.7
+// ------------------------------------------------------- Section 6.8
 void run_rowwise_qb(Ctx& c, const AMat& A, int k, int ell, const Mat& Om, Outs& o) {
   ArenaScope sc(c.ar);
   Mat Y{c.ar.take<float>(size_t(A.m) * ell), A.m, ell, A.m};
@@ -639,7 +639,7 @@ void run_rowwise_qb(Ctx& c, const AMat& A, int k, int ell, const Mat& Om, Outs& 
 // host-streamed form from column panels copied in from pinned host memory.
 using Sketcher = std::function<void(Ctx&, Mat, Mat)>;
 
-// The minimum-variance l_c of Section 6.5 from the sketches Y = A Omega
+// The minimum-variance l_c of Section 6.6 from the sketches Y = A Omega
 // (m x ell1) and Z = A^T Psi (n x ell2), left intact.  For every trial
 // l_c = 0 .. l1 the leading k singular values of X(l_c) = R^^{-1} Q^^T Z^T
 // are found, where Q^ R^ = qr(Psi^T Q_c[:, :k + l_c]) and Q_c holds the left

@@ -104,7 +104,7 @@ void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t 
 enum CholMode { CHOL_PLAIN = 0, CHOL_SHIFT_IF_NEEDED = 1, CHOL_IF_FLAGGED = 2 };
 void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int mode,
               int* needs_more, int* status, cudaStream_t s);
-// *sel = the minimum-variance l_c (Section 6.5) from nl trial spectra of k
+// *sel = the minimum-variance l_c (Section 6.6) from nl trial spectra of k
 // singular values each (lam[l_c * k + i]).
 void minvar_select(const float* lam, int nl, int k, int* sel, cudaStream_t s);
 // Racc <- R2 Racc (upper-triangular FP64, n x n); no-op when *run_if == 0.

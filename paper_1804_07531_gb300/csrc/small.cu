@@ -341,7 +341,7 @@ __global__ void upper_product_kernel(const double* __restrict__ R2, int ld2, dou
   }
 }
 
-// The minimum-variance choice of Section 6.5 from the trial spectra
+// The minimum-variance choice of Section 6.6 from the trial spectra
 // lam[l_c * k + i] (l_c = 0 .. nl - 1): for 0 <= l_c < nl - 1 the vector
 // s(l_c) = [lam(l_c - 1) / lam(l_c), 1, lam(l_c + 1) / lam(l_c)] (the first
 // block absent for l_c = 0); *sel = argmin of its population variance

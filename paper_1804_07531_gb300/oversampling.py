@@ -1,4 +1,4 @@
-"""Oversampling parameters of the single-pass method (Section 6.5).
+"""Oversampling parameters of the single-pass method (Sections 6.3 and 6.6).
 
 For a sketch budget T = 2k + l_1 + l_2 (k the target rank, the paper's p; a
 real matrix with T >= 2k + 6), the baseline single pass (Alg. 7 with

@@ -8,7 +8,7 @@ What fixes the result independently of the oracle's own code:
     (Section 4), Alg. 9 equals Alg. 2 for v < 4 (Section 7.2), the
     row-streamed block Krylov method with v views equals Alg. 9 with 2v-1
     views (Section 7.3), the row-streamed one-pass QB equals the 2-view
-    method (Section 6.7);
+    method (Section 6.8);
   * the 1-view baseline of Section 6.2 written with numpy's least squares;
   * Theorems 3.1 and 4.1 (mean spectral error below the bound) and the
     qualitative claims of Section 8 (error falls with v; block Krylov beats
@@ -69,7 +69,7 @@ def test_exact_recovery_single_pass_and_rowwise_qb():
     u, s, vv = Al.single_pass(a20, om, psi, k, l_c=0)
     assert np.abs(s - sig20).max() < 1e-10
     assert np.abs(_recon(u, s, vv) - a20).max() < 1e-10
-    # Section 6.7 needs an invertible R_c: rank(A) = ell keeps Y_c full rank.
+    # Section 6.8 needs an invertible R_c: rank(A) = ell keeps Y_c full rank.
     a30, sig30 = _lowrank(m, n, 30, seed=10)
     u, s, vv = Al.rowwise_qb_svd(a30, om, k)
     assert np.abs(s - sig30[:k]).max() < 1e-10

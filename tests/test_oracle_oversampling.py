@@ -1,4 +1,4 @@
-"""Pins for the Section 6.5 parameter rules: hand-evaluated values of the
+"""Pins for the parameter rules of Sections 6.3 (FLAT, DECAY, RAPID) and 6.6 (l_c): hand-evaluated values of the
 oversampling formulas, the package's host helpers against the oracle's own
 statement of them, and the minimum-variance selection on constructed spectra
 whose answer is known."""
@@ -55,7 +55,7 @@ def test_minvar_picks_the_flattest_neighbourhood():
 
 
 def test_minvar_on_a_rapidly_decaying_matrix_prefers_large_lc():
-    """Section 6.5: with l_1 = l_2, l_c near l_1 is ill-conditioned (large
+    """Section 6.6: with l_1 = l_2, l_c near l_1 is ill-conditioned (large
     variance) and l_c near 0 loses accuracy; the rule picks an interior
     l_c, and Alg. 7 with it is at least as accurate as with l_c = 0."""
     m, n, k = 300, 200, 5
@@ -68,3 +68,53 @@ def test_minvar_on_a_rapidly_decaying_matrix_prefers_large_lc():
     e_mv = Al.frob_error(a, u, s, v)
     u0, s0, v0 = Al.single_pass(a, om, ps, k, l_c=0)
     assert e_mv <= 1.0001 * Al.frob_error(a, u0, s0, v0)
+
+
+def _trial_spectra_by_lstsq(a, om, ps, k):
+    """Section 6.5 with each trial l_c written with library routines (test
+    only): Q_c = the leading k + l_c left singular vectors of Y_c = A Omega
+    (numpy SVD), X = the least-squares solution of (Psi^T Q_c) X = Y_r^T,
+    and the leading k singular values of X (numpy SVD)."""
+    yc, yr = a @ om, a.T @ ps
+    uy = np.linalg.svd(yc, full_matrices=False)[0]
+    rows = []
+    for lc in range(om.shape[1] - k + 1):
+        qc = uy[:, :k + lc]
+        x = np.linalg.lstsq(ps.T @ qc, yr.T, rcond=None)[0]
+        rows.append(np.linalg.svd(x, compute_uv=False)[:k])
+    return np.array(rows)
+
+
+def _spectra_with_qr_basis(a, om, ps, k):
+    """A plausible slip in minvar_spectra: Q_c from the QR of Y_c (its
+    columns span the right space only for l_c = l_1) instead of the left
+    singular vectors."""
+    yc, yr = a @ om, a.T @ ps
+    q = np.linalg.qr(yc)[0]
+    rows = []
+    for lc in range(om.shape[1] - k + 1):
+        x = np.linalg.lstsq(ps.T @ q[:, :k + lc], yr.T, rcond=None)[0]
+        rows.append(np.linalg.svd(x, compute_uv=False)[:k])
+    return np.array(rows)
+
+
+def test_minvar_spectra_rows_match_library_restatement_and_single_pass():
+    """Every row l_c of minvar_spectra is the spectrum Alg. 7 returns with that
+    l_c: against numpy's SVD / least squares, against single_pass(l_c), and
+    row l_1 against the untruncated single pass; the QR-basis slip fails."""
+    m, n, k = 180, 120, 4
+    a = S.usv(m, n, S.sigma_config("exp25", n), 11, 12) + 1e-5 * S.gaussian(m, n, seed=13)
+    om = S.gaussian(n, k + 6, seed=14)
+    ps = S.gaussian(m, k + 9, seed=15)
+    spec = Al.minvar_spectra(a, om, ps, k)
+    assert spec.shape == (7, k)
+    ref = _trial_spectra_by_lstsq(a, om, ps, k)
+    assert np.max(np.abs(spec - ref) / ref[:, :1]) < 1e-10
+    for lc in range(7):
+        s_lc = Al.single_pass(a, om, ps, k, l_c=lc)[1]
+        assert np.max(np.abs(spec[lc] - s_lc)) < 1e-10 * s_lc[0]
+    s_full = Al.single_pass(a, om, ps, k)[1]
+    assert np.max(np.abs(spec[-1] - s_full)) < 1e-10 * s_full[0]
+    slip = _spectra_with_qr_basis(a, om, ps, k)
+    assert np.max(np.abs(slip[-1] - ref[-1]) / ref[-1, 0]) < 1e-10   # same span at l_c = l_1
+    assert np.max(np.abs(slip[:-1] - ref[:-1]) / ref[:-1, :1]) > 1e-4  # differs below l_1
