@@ -70,7 +70,7 @@ typedef struct {
   int32_t col_major; /* 1 column-major, 0 row-major */
 } lr_mat;
 
-/* lr_opts.l_c value: choose l_c by the minimum-variance rule of Section 6.5. */
+/* lr_opts.l_c value: choose l_c by the minimum-variance rule of Section 6.6. */
 #define LR_LC_MINVAR (-2)
 
 /* Options; zero-initialise for defaults. */
@@ -81,8 +81,12 @@ typedef struct {
                                synchronises its stream once, as the choice sizes the rest) */
   int32_t enhanced;         /* lr_block_krylov: 1 = row-streamed variant of Section 7.3 */
   int32_t split_last;       /* BF16 form: last view's operand as BF16 hi + lo (two products) */
-  int32_t shifted_fallback; /* kept for compatibility: every thin QR already retries a
-                               breakdown with a shifted Gram (shifted CholeskyQR3) */
+  int32_t shifted_fallback; /* 0: every thin QR retries a Cholesky breakdown of its first
+                               pass with a shifted Gram and adds a third pass (shifted
+                               CholeskyQR3): full-rank sketches up to kappa ~ 1e7.  1: also
+                               rank-deficient sketches (A of rank below k + p): a flagged
+                               block takes shifted, shifted, plain, plain passes; without
+                               it such a sketch ends in LR_ERR_BREAKDOWN */
   int32_t band_mb;          /* one-read sketches (dual, chained): MiB of A per L2 band;
                                0 = default; a value >= the size of A means two full passes */
   int32_t reserved[3];
@@ -111,7 +115,7 @@ lr_status lr_set_workspace(lr_handle handle, void* dev_ptr, size_t bytes);
  * *device_status and clear it. */
 lr_status lr_get_status(lr_handle handle, void* stream, int* device_status);
 
-/* One view of A (Section 4 and Alg. 2; the sketches of Section 6.4, Alg. 7):
+/* One view of A (Section 4 and Alg. 2; the sketches of Section 6.5, Alg. 7):
  *   Y = A X   (X: n x ell1, Y: m x ell1) when X != NULL,
  *   Z = A^T W (W: m x ell2, Z: n x ell2) when W != NULL.
  * With both X and W the two products share one read of A from HBM (the
@@ -120,7 +124,7 @@ lr_status lr_get_status(lr_handle handle, void* stream, int* device_status);
 lr_status lr_sketch(lr_handle handle, const lr_mat* A, const lr_mat* X, const lr_mat* W,
                     lr_mat* Y, lr_mat* Z, const lr_opts* opts, void* stream);
 
-/* Chained view (Section 6.7): Y = A X and Z = A^T Y from one read of A.
+/* Chained view (Section 6.8): Y = A X and Z = A^T Y from one read of A.
  * Same argument rules as lr_sketch; Y and Z are overwritten. */
 lr_status lr_sketch_chained(lr_handle handle, const lr_mat* A, const lr_mat* X, lr_mat* Y,
                             lr_mat* Z, const lr_opts* opts, void* stream);
@@ -143,7 +147,7 @@ lr_status lr_subspace_iter(lr_handle handle, const lr_mat* A, int k, int p, int 
                            const lr_mat* Omega, lr_mat* U, lr_mat* S, lr_mat* V,
                            const lr_opts* opts, void* stream);
 
-/* Single-pass TSVD, Alg. 7 (Section 6.4, Tropp variant): Omega n x ell1,
+/* Single-pass TSVD, Alg. 7 (Section 6.5, Tropp variant): Omega n x ell1,
  * Psi m x ell2 with ell2 >= ell1 > k; opts->l_c in [0, ell1 - k] truncates
  * Q_c to its leading k + l_c left singular vectors (l_c < 0: none, the
  * baseline of Section 6.2).  Both sketches come from one read of A. */
@@ -159,7 +163,7 @@ lr_status lr_block_krylov(lr_handle handle, const lr_mat* A, int k, int p, int v
                           const lr_mat* Omega, lr_mat* U, lr_mat* S, lr_mat* V,
                           const lr_opts* opts, void* stream);
 
-/* Row-streamed one-pass QB of Section 6.7: Y = A Omega and A^T Y from one
+/* Row-streamed one-pass QB of Section 6.8: Y = A Omega and A^T Y from one
  * read, Q_c R_c = Y, B^T = (A^T Y) R_c^{-1}, then the TSVD of B. */
 lr_status lr_rowwise_single_pass(lr_handle handle, const lr_mat* A, int k, const lr_mat* Omega,
                                  lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts,
@@ -235,23 +239,38 @@ lr_status lr_selftest_bounded_wait(lr_handle handle, int64_t timeout_us, void* s
  * Allocation-free range view (the paper has no counterpart).
  * ------------------------------------------------------------------- */
 
-/* Y = A X exactly as lr_sketch computes it with W = NULL, for callers that
- * cannot call cudaMalloc at all -- e.g. a host program whose own pool has
- * reserved the device's memory, or one that cannot accept the device-wide
+/* Y = A X as lr_sketch computes it with W = NULL, for callers that cannot
+ * call cudaMalloc at all -- e.g. a host program whose own pool has reserved
+ * the device's memory, or one that cannot accept the device-wide
  * synchronisation a cudaMalloc may imply -- and therefore cannot create an
  * lr_handle or provide a workspace.  No handle is needed and nothing is
  * allocated: the BF16 copy of X that the tensor-core kernel reads lives in a
- * 4 MiB file-scope device array (held on every GPU that loads the library
- * until the library is unloaded), so ceil8(n) * ell * 2 bytes must fit in
- * 4 MiB minus 256 bytes (else LR_ERR_UNSUPPORTED), and ell <= 256.  An F32 A
- * needs no scratch.  Arguments as for lr_sketch; runs on the current device
- * and `stream`.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture begins.  All calls share the array: calls that overlap on the GPU
- * (other streams or host threads on the same device) race and must be
- * serialised by the caller.  Device-side timeouts are not reported (there is
- * no handle to hold a status); argument errors are returned synchronously. */
+ * 4 MiB file-scope device array, so ceil8(n) * ell * 2 bytes must fit in
+ * 4 MiB minus 256 bytes (else LR_ERR_UNSUPPORTED), and ell <= 256.  For a
+ * BF16 A the view is lr_sketch's own tensor-core kernel.  An F32 A needs no
+ * scratch: it runs on the SIMT GEMM and matches lr_sketch (3xTF32) to within
+ * the view tolerance, not bit for bit.  Arguments as for lr_sketch; runs on
+ * the current device and `stream`.
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture
+ * begins.  Under lazy module loading (the CUDA default) that first call is
+ * also when the runtime loads this code and reserves the 4 MiB on the
+ * device (held until the process exits), so a caller whose pool will claim
+ * the device's memory makes the first call at start-up, or sets
+ * CUDA_MODULE_LOADING=EAGER.
+ * All calls share the array: calls that overlap on the GPU (other streams
+ * or host threads on the same device) race and must be serialised by the
+ * caller.  Argument errors are returned synchronously; a device-side
+ * failure (a bounded wait that ran out: LR_ERR_TIMEOUT) is kept in the
+ * array's status word, which every call clears at its start and
+ * lr_sketch_range_static_status reads. */
 lr_status lr_sketch_range_static(const lr_mat* A, const lr_mat* X, lr_mat* Y, void* stream);
+
+/* The device status word of the latest lr_sketch_range_static call on the
+ * current device (0 or an lr_status code), copied to *device_status after
+ * `stream` has finished that call (synchronises `stream`).  Allocates
+ * nothing. */
+lr_status lr_sketch_range_static_status(void* stream, int* device_status);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,7 @@ EXPORTS = [
     "lr_set_workspace", "lr_get_status", "lr_sketch", "lr_sketch_chained", "lr_orth",
     "lr_subspace_iter", "lr_single_pass", "lr_block_krylov", "lr_rowwise_single_pass",
     "lr_single_pass_host", "lr_subspace_iter_host", "lr_subspace_iter_backward", "lr_set_trace", "lr_trace_read",
-    "lr_kernel_launches", "lr_sketch_range_static", "lr_selftest_bounded_wait",
+    "lr_kernel_launches", "lr_sketch_range_static", "lr_sketch_range_static_status", "lr_selftest_bounded_wait",
 ]
 TRACE_KINDS = {"view_range": 0, "view_corange": 1, "orth": 2, "core_svd": 3}
 
@@ -93,6 +93,7 @@ def lib():
             L.lr_trace_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I]
             L.lr_kernel_launches.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]
             L.lr_sketch_range_static.argtypes = [M, M, M, P]
+            L.lr_sketch_range_static_status.argtypes = [P, ctypes.POINTER(I)]
             L.lr_selftest_bounded_wait.argtypes = [P, I64, P]
             for name in EXPORTS:
                 f = getattr(L, name)

@@ -143,7 +143,7 @@ def rowwise_single_pass(a, k, omega, stream=None):
     return u, s, vv
 
 
-def single_pass(a, k, omega, psi, l_c=None, stream=None):
+def single_pass(a, k, omega, psi, l_c=None, shifted_fallback=False, stream=None):
     """Alg. 7: 1-view TSVD.  l_c=None: the baseline (l_c = l_1); an int
     0 <= l_c <= l_1 (e.g. oversampling.fixed_ratio(l_1, 0.5)); "minvar": the
     minimum-variance rule of Section 6.6, chosen on the device from the
@@ -154,7 +154,7 @@ def single_pass(a, k, omega, psi, l_c=None, stream=None):
     h.reserve(m, n, omega.shape[1], psi.shape[1], 1)
     u, s, vv = _outs(a, k)
     mats = [mat_a(a), mat_thin(omega), mat_thin(psi), mat_thin(u), mat_thin(s), mat_thin(vv)]
-    o = _opts(l_c=l_c)
+    o = _opts(l_c=l_c, shifted_fallback=shifted_fallback)
     _call(h, lib().lr_single_pass, _p(mats[0]), k, _p(mats[1]), _p(mats[2]), _p(mats[3]), _p(mats[4]),
           _p(mats[5]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return u, s, vv

@@ -124,7 +124,7 @@ void gemm(Ctx& c, int64_t M, int64_t N, int64_t K, bool ta, const float* A, int6
     float* wl = c.ar.take<float>(size_t(ldw) * N);
     if (c.measure) return;
     split_tf32(B, ldb, wh, wl, ldw, K, N, c.s, alpha);
-    if (beta == 0.f) zero_f32(C, M, N, ldc, c.s);  // (a skipped launch leaves only scratch zeroed)
+    if (beta == 0.f) zero_f32(C, M, N, ldc, c.s, run_if);  // a skipped product leaves C as it was
     ViewTf32Args a;
     a.device = c.h->device;
     a.mode = 1;
@@ -412,7 +412,14 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0) {
     // Fukaya et al. 2020): pass 1 is plain, or shifted when the plain
     // Cholesky breaks down -- which happens in FP32 once kappa(Y_b) nears
     // 1e3 -- and then flags a third pass that the device runs only if set.
-    // Passes alternate Y_b -> T -> Y_b -> T; R_bb = R_last ... R_1.
+    // With opts.shifted_fallback (rank-deficient input: a sketch of a matrix
+    // of rank below the block's width) a flagged block takes four passes:
+    // shifted, shifted again (the directions outside the column space are
+    // still below the FP32 Cholesky's resolution after one shift), then two
+    // plain passes that make every column orthonormal; Y_b = Q R holds
+    // exactly through shifted passes, so R stays the triangular factor.
+    // Passes alternate Y_b -> T -> Y_b -> T (-> Y_b); R_bb = R_last ... R_1.
+    const bool robust = c.opt.shifted_fallback != 0;
     double* Rbb = R ? R + c0 + int64_t(c0) * L : nullptr;
     // pass 1: Y_b -> T
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w);
@@ -420,7 +427,8 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0) {
     gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m);
     // pass 2: T -> Y_b (R_bb <- R_2 R_bb by a separate many-CTA product)
     gram64(c, w, w, m, T, m, T, m, G64, w);
-    chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_PLAIN, more, c.status, c.s);
+    chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, robust ? CHOL_SHIFT_IF_FLAGGED : CHOL_PLAIN, more,
+             c.status, c.s);
     if (Rbb) upper_product(R2, w, Rbb, L, w, nullptr, c.s);
     gemm(c, m, w, w, false, T, m, false, Rinv, w, Yb, Y.ld);
     // pass 3 (only after a shifted pass 1): Y_b -> T -> Y_b
@@ -428,7 +436,15 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0) {
     chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_IF_FLAGGED, more, c.status, c.s);
     if (Rbb) upper_product(R2, w, Rbb, L, w, more, c.s);
     gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m, 1.f, 0.f, more);
-    copy_f32(T, m, Yb, Y.ld, m, w, c.s, more);
+    if (robust) {
+      // pass 4: T -> Y_b
+      gram64(c, w, w, m, T, m, T, m, G64, w, more);
+      chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_IF_FLAGGED, more, c.status, c.s);
+      if (Rbb) upper_product(R2, w, Rbb, L, w, more, c.s);
+      gemm(c, m, w, w, false, T, m, false, Rinv, w, Yb, Y.ld, 1.f, 0.f, more);
+    } else {
+      copy_f32(T, m, Yb, Y.ld, m, w, c.s, more);
+    }
     c0 += w;
   }
 }

@@ -244,11 +244,15 @@ __device__ __forceinline__ void block_inverse_offdiag(const float* L, float* X, 
 //                            shifted CholeskyQR (Fukaya et al. 2020),
 //                            1e-5 trace(G), and set *needs_more = 1 so the
 //                            caller's optional pass runs;
+//       CHOL_SHIFT_IF_FLAGGED the shifted factorisation when *needs_more != 0
+//                            (the pass after a shifted one, for
+//                            rank-deficient input), the plain one otherwise;
 //       CHOL_IF_FLAGGED      run only when *needs_more != 0 (else nothing).
 __global__ void __launch_bounds__(kThreadsC) chol_inv_kernel(const double* __restrict__ G, int n, float* Rinv,
                                                              int ldr, double* Racc, int ldacc, int init_acc, int mode,
                                                              int* needs_more, int* status) {
-  if (mode == CHOL_IF_FLAGGED && (needs_more == nullptr || *needs_more == 0)) return;
+  const bool flagged = needs_more != nullptr && *needs_more != 0;
+  if (mode == CHOL_IF_FLAGGED && !flagged) return;
   extern __shared__ float sm[];
   const int N = (n + kB - 1) / kB * kB, ld = N + 1;
   float* A = sm;
@@ -290,7 +294,8 @@ __global__ void __launch_bounds__(kThreadsC) chol_inv_kernel(const double* __res
     return;
   }
   bool broke = false, shifted = false;
-  for (int attempt = 0; attempt < 2; ++attempt) {
+  const bool shift_first = mode == CHOL_SHIFT_IF_FLAGGED && flagged;
+  for (int attempt = shift_first ? 1 : 0; attempt < 2; ++attempt) {
     if (attempt == 1) {
       shifted = true;
       // the shift sits above the FP32 Gram and Cholesky rounding level, so
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(kThreadsC) chol_inv_kernel(const double* __res
     broke = block_cholesky(A, L, X, N, ld, &bad, colbuf);
     if (!broke || mode != CHOL_SHIFT_IF_NEEDED) break;
   }
-  if (!broke && shifted && tid == 0 && needs_more) *needs_more = 1;
+  if (!broke && shifted && mode == CHOL_SHIFT_IF_NEEDED && tid == 0 && needs_more) *needs_more = 1;
   if (broke) {
     if (tid == 0) set_status(status, LR_ERR_BREAKDOWN);
     // leave a harmless identity so later kernels stay finite

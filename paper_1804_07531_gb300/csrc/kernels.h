@@ -84,7 +84,8 @@ void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd
                 cudaStream_t s, float scale = 1.f);
 
 // ---------------------------------------------------------- elementwise
-void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s);
+// run_if (device int, optional): zero only when *run_if != 0.
+void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s, const int* run_if = nullptr);
 void zero_bytes(void* p, size_t bytes, cudaStream_t s);
 // dst (bf16, col-major rows x cols, ldd) = round(src); with lo != nullptr
 // also lo = round(src - hi) (the hi/lo split of a thin operand).
@@ -101,7 +102,7 @@ void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t 
 //   G (ell x ell, FP64 col-major, ld ell) = R^T R; writes Rinv (FP32,
 //   ell x ell, ldr); Racc (FP64, ldacc) <- R (init_acc) or R * Racc.
 //   Racc may be nullptr.  Breakdown / non-finite -> status.
-enum CholMode { CHOL_PLAIN = 0, CHOL_SHIFT_IF_NEEDED = 1, CHOL_IF_FLAGGED = 2 };
+enum CholMode { CHOL_PLAIN = 0, CHOL_SHIFT_IF_NEEDED = 1, CHOL_IF_FLAGGED = 2, CHOL_SHIFT_IF_FLAGGED = 3 };
 void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int mode,
               int* needs_more, int* status, cudaStream_t s);
 // *sel = the minimum-variance l_c (Section 6.6) from nl trial spectra of k

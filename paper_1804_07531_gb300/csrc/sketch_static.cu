@@ -7,8 +7,9 @@
 // a workspace, so they cannot use lr_sketch.  This entry point serves them:
 // the only scratch the range view needs -- the BF16 copy of the thin operand
 // X that the tensor-core kernel reads through TMA, plus a status word -- lives
-// in a file-scope __device__ array that the CUDA runtime reserves on every GPU
-// that loads this library, for as long as the library stays loaded.
+// in a file-scope __device__ array that the CUDA runtime reserves on a GPU
+// when this code is loaded there (see below) and holds until the process
+// exits.
 //
 // The array's host-side name is only a stand-in for the device symbol, so the
 // device address is obtained once per device with cudaGetSymbolAddress (with
@@ -18,7 +19,17 @@
 // overlap on the GPU (different streams, or different host threads on the
 // same device) race on it and must be serialised by the caller.  A later call
 // overwrites what an earlier call left there; the status word is cleared at
-// the start of every call.
+// the start of every call and read back by lr_sketch_range_static_status.
+//
+// With lazy module loading (the CUDA default since 12.2) the array and this
+// file's kernels are brought onto a device by the first call there, not when
+// the library is loaded: that first call is where the runtime reserves the
+// 4 MiB, so a caller whose pool later claims the device's memory makes it at
+// start-up (or runs with CUDA_MODULE_LOADING=EAGER).
+//
+// For an F32 A the view runs on the SIMT GEMM (no scratch at all) and agrees
+// with lr_sketch's 3xTF32 tensor-core view to within the view tolerance, not
+// bit for bit; for a BF16 A it runs lr_sketch's own kernel.
 #include <mutex>
 
 #include "common.cuh"
@@ -112,6 +123,24 @@ extern "C" lr_status lr_sketch_range_static(const lr_mat* A, const lr_mat* X, lr
       g.split_k = split_for(m, ell, n, dev_info(device).sms);
       sgemm(g, s);
     }
+    return LR_OK;
+  } catch (const Error& e) {
+    return e.st;
+  }
+}
+
+extern "C" lr_status lr_sketch_range_static_status(void* stream, int* device_status) {
+  using namespace lr;
+  try {
+    LR_REQUIRE(device_status, LR_ERR_INVALID_ARG, "device_status is NULL");
+    int device = 0;
+    LR_CHECK_CUDA(cudaGetDevice(&device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char* base = static_cast<const char*>(scratch_for(device));
+    int v = 0;
+    LR_CHECK_CUDA(cudaMemcpyAsync(&v, base + kStatusOffset, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LR_CHECK_CUDA(cudaStreamSynchronize(s));
+    *device_status = v;
     return LR_OK;
   } catch (const Error& e) {
     return e.st;

@@ -387,8 +387,20 @@ void upper_product(const double* R2, int ld2, double* Racc, int ldr, int n, cons
   LR_LAUNCH_CHECK();
 }
 
-void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s) {
+__global__ void zero_if_kernel(float* __restrict__ p, int64_t ld, int64_t rows, int64_t cols, const int* run_if) {
+  if (*run_if == 0) return;
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x)
+      p[r + c * ld] = 0.f;
+}
+
+void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s, const int* run_if) {
   if (rows <= 0 || cols <= 0) return;
+  if (run_if) {
+    zero_if_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(p, ld, rows, cols, run_if);
+    LR_LAUNCH_CHECK();
+    return;
+  }
   if (ld == rows) {
     LR_CHECK_CUDA(cudaMemsetAsync(p, 0, size_t(rows) * cols * sizeof(float), s));
   } else {
