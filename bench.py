@@ -182,6 +182,60 @@ def _peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+# ------------------------------------------------------- dual sketch
+DUAL_WIDTHS = ((32, 64), (120, 240))
+
+
+def dual_sketch_cases(a, hbm, bf16_pk, reps=10):
+    """The one-read dual sketch Y = A X, Z = A^T W (Alg. 7 steps a, b) on the
+    workload's matrix: the fused kernel (each staged tile of A feeds both
+    products, A read once) against two full passes, at a narrow width pair
+    and at the single-pass workload's (ell1, ell2) = (120, 240).  Kernel times
+    come from the library's CUDA-event trace; call times include the operand
+    conversion and output zeroing."""
+    import torch
+
+    from paper_1804_07531_gb300 import api
+    from paper_1804_07531_gb300._binding import Handle
+    h = Handle.get(a.device)
+    m, n = a.shape
+    a_bytes = a.numel() * a.element_size()
+    gen = torch.Generator(device=a.device)
+    gen.manual_seed(31)
+    out = {}
+    for ell1, ell2 in DUAL_WIDTHS:
+        x = torch.randn(n, ell1, generator=gen, device=a.device)
+        w = torch.randn(m, ell2, generator=gen, device=a.device)
+        res = {"default": "fused" if ell2 <= 64 else "two_pass"}
+        flops = 2.0 * m * n * (ell1 + ell2)
+        for name, band in (("fused", -2), ("two_pass", -1)):
+            for _ in range(2):
+                api.sketch(a, x, w, band_mb=band)
+            torch.cuda.synchronize()
+            h.set_trace(True)
+            h.trace_read("view_range", reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                api.sketch(a, x, w, band_mb=band)
+            e1.record()
+            torch.cuda.synchronize()
+            d_ms, d_n = h.trace_read("view_dual")
+            r_ms, r_n = h.trace_read("view_range")
+            c_ms, c_n = h.trace_read("view_corange", reset=True)
+            h.set_trace(False)
+            k_ms = (d_ms + r_ms + c_ms) / reps
+            res[name] = {
+                "ms_call": round(e0.elapsed_time(e1) / reps, 4), "ms_kernels": round(k_ms, 4),
+                "kernel_launches": int((d_n + r_n + c_n) // reps), "a_reads": 1 if name == "fused" else 2,
+                "a_gbs": round(a_bytes / (k_ms * 1e-3) / 1e9, 1),
+                "frac_hbm": round(a_bytes / (k_ms * 1e-3) / 1e9 / hbm, 4),
+                "frac_tensor": round(flops / (k_ms * 1e-3) / 1e12 / bf16_pk, 4),
+            }
+        out[f"ell1_{ell1}_ell2_{ell2}"] = res
+    return out
+
+
 # --------------------------------------------------------- CPU baseline
 CPU_ROWS = 1024
 
@@ -281,6 +335,10 @@ def run_ours(args):
     ms_max = _max_over_ranks(dist, ms_step, dev)
     total_bytes = _sum_over_ranks(dist, VIEWS * a_bytes * args.steps, dev)
     value = total_bytes / (ms_max * args.steps * 1e-3) / 1e9
+
+    # ---- the one-read dual sketch on the same matrix
+    hbm0, bf16_pk0, _ = _peaks()
+    dual = dual_sketch_cases(a, hbm0, bf16_pk0) if rank == 0 else None
 
     # ---- accuracy of the BF16 form, and the FP32 form at equal error
     e_bf16 = recon_error(a, u, s, v)
@@ -384,6 +442,7 @@ def run_ours(args):
             "ms_per_step": round(ms_fp32, 3), "recon_error": e_fp32, "bf16_recon_error": e_bf16,
             "bf16_over_fp32_error": e_bf16 / e_fp32, "bf16_speedup": ms_fp32 / ms_max,
         },
+        "dual_sketch": dual,
         "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t_e2e * 1e3, 3)},
         "gpu_launches": int(launches),
@@ -449,10 +508,10 @@ def run_case(args):
         w2 = torch.randn(m, 2 * ell, generator=gen, device=dev)
 
         def call():
-            return api.sketch(a, x, w2)
+            return api.sketch(a, x, w2, band_mb=args.case_band)
     elif case in ("chained_bf16", "chained_f32"):
         def call():
-            return api.sketch_chained(a, x)
+            return api.sketch_chained(a, x, band_mb=args.case_band)
     elif case == "orth":
         y = torch.randn(m, ell, generator=gen, device=dev)
 
@@ -489,7 +548,8 @@ def run_case(args):
         raise RuntimeError(f"device status {st}")
     ms = statistics.median(times)
     a_bytes = a.numel() * a.element_size()
-    print(json.dumps({"case": case, "m": m, "n": n, "ell": ell, "a_dtype": str(a.dtype).split(".")[-1],
+    print(json.dumps({"case": case, "band_mb": args.case_band, "m": m, "n": n, "ell": ell,
+                      "a_dtype": str(a.dtype).split(".")[-1],
                       "ms_median": round(ms, 4), "a_gbs": round(a_bytes / (ms * 1e-3) / 1e9, 1),
                       "reps": args.case_reps}), flush=True)
 
@@ -570,6 +630,9 @@ def main():
     ap.add_argument("--case-n", type=int, default=16384)
     ap.add_argument("--case-ell", type=int, default=120)
     ap.add_argument("--case-reps", type=int, default=3)
+    ap.add_argument("--case-band", type=int, default=0,
+                    help="opts.band_mb for the dual/chained cases: 0 fused one-read kernel where available, "
+                         "-1 two full passes, > 0 L2 bands of that many MiB")
     args = ap.parse_args()
     if args.kernel_case == "host_stream":
         run_host_case(args)

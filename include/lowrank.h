@@ -87,8 +87,13 @@ typedef struct {
                                rank-deficient sketches (A of rank below k + p): a flagged
                                block takes shifted, shifted, plain, plain passes; without
                                it such a sketch ends in LR_ERR_BREAKDOWN */
-  int32_t band_mb;          /* one-read sketches (dual, chained): MiB of A per L2 band;
-                               0 = default; a value >= the size of A means two full passes */
+  int32_t band_mb;          /* one-read sketches (dual, chained): 0 = default: the dual
+                               sketch of a BF16 A with ell1 <= 128 and ell2 <= 64 runs the
+                               fused kernel that feeds each staged tile of A to both
+                               products (A read once), other widths two full passes;
+                               -2 = the fused kernel whenever ell1 <= 128, ell2 <= 256;
+                               -1 = two full passes; > 0 = L2 bands of that many MiB of
+                               A, each read by the two products back to back */
   int32_t reserved[3];
 } lr_opts;
 
@@ -211,7 +216,8 @@ typedef enum {
   LR_TRACE_VIEW_CORANGE = 1, /* Z = A^T W                                          */
   LR_TRACE_ORTH = 2,         /* one lr_orth-equivalent thin QR (all its kernels)    */
   LR_TRACE_CORE_SVD = 3,     /* the small core SVD                                  */
-  LR_TRACE_COUNT = 4
+  LR_TRACE_VIEW_DUAL = 4,    /* Y = A X and Z = A^T W in one pass (fused kernel)    */
+  LR_TRACE_COUNT = 5
 } lr_trace_kind;
 
 /* Turn per-launch CUDA-event timing of the classes above on (1) or off (0).

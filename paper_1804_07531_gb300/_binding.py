@@ -33,7 +33,7 @@ EXPORTS = [
     "lr_single_pass_host", "lr_subspace_iter_host", "lr_subspace_iter_backward", "lr_set_trace", "lr_trace_read",
     "lr_kernel_launches", "lr_sketch_range_static", "lr_sketch_range_static_status", "lr_selftest_bounded_wait",
 ]
-TRACE_KINDS = {"view_range": 0, "view_corange": 1, "orth": 2, "core_svd": 3}
+TRACE_KINDS = {"view_range": 0, "view_corange": 1, "orth": 2, "core_svd": 3, "view_dual": 4}
 
 
 class LrMat(ctypes.Structure):

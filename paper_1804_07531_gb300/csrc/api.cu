@@ -295,7 +295,7 @@ void view_band(Ctx& c, const AMat& A, int mode, const float* B, int64_t ldb, int
 int64_t band_rows(const AMat& A, int band_mb) {
   // band_mb > 0: bands of that many MiB of A, each read by the range and the
   // co-range products back to back so the second read hits L2 (129 MB).
-  // Default (0): one band, i.e. two full passes over A.  Measured on GB300
+  // Otherwise (0, -1): one band, i.e. two full passes over A.  Measured on GB300
   // for a 2 GiB A: two full passes (each near the HBM roof) beat every band
   // size, because each band costs two launches and partial-tile atomics
   // that outweigh the HBM bytes saved.
@@ -317,9 +317,15 @@ void view_corange(Ctx& c, const AMat& A, const Mat& W, Mat Z, bool last = false)
   view_band(c, A, 1, W.p, W.ld, int(W.cols), Z.p, Z.ld, 0, A.m, nullptr, last && c.opt.split_last && A.bf16);
 }
 
-// Y = A X and Z = A^T W (the two sketches of Alg. 7).  The operands are
-// converted once; the bands of band_rows() are swept by the range and then
-// the co-range kernel (by default one band: two full passes over A).
+// Y = A X and Z = A^T W (the two sketches of Alg. 7, steps a and b).  The
+// operands are converted once.  For a BF16 A the fused kernel reads A once,
+// each staged tile feeding both products; it flushes a partial Z^T per tile
+// of 256 rows, ell2 / 64 bytes of L2 reductions per element of A, which L2
+// absorbs at about the HBM rate (measured), so it wins where that is below
+// the 2 bytes of the second read it saves: by default it runs for
+// ell2 <= 64 (and ell1 <= 128); opts.band_mb = -2 forces it (ell2 <= 256),
+// -1 forces two passes.  Otherwise the range and co-range kernels sweep the
+// bands of band_rows() (by default one band: two full passes over A).
 void view_dual(Ctx& c, const AMat& A, const Mat& X, Mat Y, const Mat& W, Mat Z) {
   ArenaScope sc(c.ar);
   const SplitOp xo = convert_operand(c, A, X.p, X.ld, A.n, int(X.cols));
@@ -327,6 +333,30 @@ void view_dual(Ctx& c, const AMat& A, const Mat& X, Mat Y, const Mat& W, Mat Z) 
   if (c.measure) return;
   zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
   zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
+  const bool fused = A.bf16 && dual_bf16_supported(int(X.cols), int(W.cols)) &&
+                     (c.opt.band_mb == -2 || (c.opt.band_mb == 0 && W.cols <= 64));
+  if (fused) {
+    TraceScope tr(c, LR_TRACE_VIEW_DUAL);
+    DualBf16Args d;
+    d.device = c.h->device;
+    d.A = A.b();
+    d.lda = A.ld;
+    d.m = A.m;
+    d.n = A.n;
+    d.X = xo.bf;
+    d.ldx = xo.ld;
+    d.ell1 = int(X.cols);
+    d.W = wo.bf;
+    d.ldw = wo.ld;
+    d.ell2 = int(W.cols);
+    d.Y = Y.p;
+    d.ldy = Y.ld;
+    d.Z = Z.p;
+    d.ldz = Z.ld;
+    d.status = c.status;
+    view_dual_bf16(d, c.s);
+    return;
+  }
   const int64_t rb = band_rows(A, c.opt.band_mb);
   for (int64_t r0 = 0; r0 < A.m; r0 += rb) {
     const int64_t rows = std::min(rb, A.m - r0);

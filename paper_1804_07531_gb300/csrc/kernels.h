@@ -41,6 +41,28 @@ struct ViewBf16Args {
   int* status = nullptr;
 };
 void view_bf16(const ViewBf16Args& a, cudaStream_t s);
+
+// Y = A X and Z = A^T W from one pass over a BF16 A (each staged tile of A
+// feeds both products); Y and Z are zeroed by the caller and receive FP32
+// sums.  X (n x ell1) and W (m x ell2) are BF16 column-major.
+struct DualBf16Args {
+  int device = 0;
+  const __nv_bfloat16* A = nullptr;
+  int64_t lda = 0, m = 0, n = 0;
+  const __nv_bfloat16* X = nullptr;
+  int64_t ldx = 0;
+  int ell1 = 0;
+  const __nv_bfloat16* W = nullptr;
+  int64_t ldw = 0;
+  int ell2 = 0;
+  float* Y = nullptr;
+  int64_t ldy = 0;
+  float* Z = nullptr;
+  int64_t ldz = 0;
+  int* status = nullptr;
+};
+bool dual_bf16_supported(int ell1, int ell2);
+void view_dual_bf16(const DualBf16Args& a, cudaStream_t s);
 int view_bf16_ncol(int ell);
 
 // FP32 form on the tensor cores (3xTF32).  The thin operand is given split:

@@ -22,145 +22,16 @@
 // Every mbarrier wait is bounded (about 2 s of %globaltimer); on expiry the
 // kernel records LR_ERR_TIMEOUT, lets in-flight copies and MMAs finish,
 // frees its TMEM and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
 #include <algorithm>
-#include <mutex>
 
-#include "common.cuh"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace lr {
 namespace {
 
-constexpr uint64_t kTimeoutNs = 2000000000ull;
+using namespace tc;
 constexpr int kThreads = 192;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase with the given parity.  Returns false when the
-// CTA is aborting (another role timed out) or this wait timed out.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (globaltimer() - t0 > kTimeoutNs) {
-      *abort_flag = 1;
-      set_status(status, LR_ERR_TIMEOUT);
-      return false;
-    }
-  }
-}
-// mbar_wait for roles in which all 32 lanes wait: a lane that gives up just
-// before the phase completes makes the whole warp give up, so the warp stays
-// converged for the .sync.aligned instructions and __syncwarp that follow.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  const bool ok = mbar_wait(bar, parity, abort_flag, status);
-  return __all_sync(0xffffffffu, ok);
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// tcgen05 shared-memory matrix descriptor, 128-byte swizzle (sm_100 family):
-// start address >> 4 in bits 0-13, leading byte offset >> 4 in bits 16-29,
-// stride byte offset >> 4 in bits 32-45, descriptor version 1 at bit 46,
-// layout type 2 (SWIZZLE_128B) in bits 61-63.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = uint64_t((saddr & 0x3FFFFu) >> 4);
-  d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
-  d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
-  d |= 1ull << 46;
-  d |= 2ull << 61;
-  return d;
-}
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), A major (bit 15: 0 K-major, 1 MN-major), B K-major,
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool a_mn_major) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t(n) >> 3) << 17) |
-         ((128u >> 4) << 24);
-}
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum));
-}
-// kind::tf32: A = B = TF32 (format 2 in bits 7-9, 10-12), D = F32.
-__host__ __device__ constexpr uint32_t idesc_tf32(int n, bool a_mn_major) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((a_mn_major ? 1u : 0u) << 15) | ((uint32_t(n) >> 3) << 17) |
-         ((128u >> 4) << 24);
-}
-__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accum));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
-      : "memory");
-}
 
 struct ViewParams {
   int64_t m_out;        // valid output rows
@@ -669,38 +540,6 @@ __global__ void split_tf32_kernel(const float* __restrict__ src, int64_t lds, fl
 }
 
 // ------------------------------------------------------------------ host
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-  });
-  LR_REQUIRE(fn != nullptr, LR_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-  return fn;
-}
-
-// 2-D BF16 tensor map over a row-major (dim1 x dim0) array with row stride
-// ld elements, box (box0 x box1), 128-byte swizzle, zero fill out of bounds.
-CUtensorMap make_map_bf16(const void* base, int64_t dim0, int64_t dim1, int64_t ld, int box0, int box1) {
-  LR_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, LR_ERR_ALIGNMENT, "TMA base not 16-byte aligned");
-  LR_REQUIRE((ld * 2) % 16 == 0, LR_ERR_ALIGNMENT, "TMA row stride not a multiple of 16 bytes");
-  CUtensorMap m;
-  cuuint64_t dims[2] = {cuuint64_t(dim0), cuuint64_t(dim1)};
-  cuuint64_t strides[1] = {cuuint64_t(ld * 2)};
-  cuuint32_t box[2] = {cuuint32_t(box0), cuuint32_t(box1)};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  LR_REQUIRE(r == CUDA_SUCCESS, LR_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
-  return m;
-}
-
 template <int MODE, int NCOL>
 void launch_ncol(const CUtensorMap& ma, const CUtensorMap& mb, ViewParams p, int tiles, int sms, cudaStream_t s) {
   constexpr int NS = 2;
@@ -770,21 +609,6 @@ void view_bf16(const ViewBf16Args& a, cudaStream_t s) {
 
 
 namespace {
-CUtensorMap make_map_f32(const void* base, int64_t dim0, int64_t dim1, int64_t ld, int box0, int box1) {
-  LR_REQUIRE((reinterpret_cast<uintptr_t>(base) & 15) == 0, LR_ERR_ALIGNMENT, "TMA base not 16-byte aligned");
-  LR_REQUIRE((ld * 4) % 16 == 0, LR_ERR_ALIGNMENT, "TMA row stride not a multiple of 16 bytes");
-  CUtensorMap m;
-  cuuint64_t dims[2] = {cuuint64_t(dim0), cuuint64_t(dim1)};
-  cuuint64_t strides[1] = {cuuint64_t(ld * 4)};
-  cuuint32_t box[2] = {cuuint32_t(box0), cuuint32_t(box1)};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  LR_REQUIRE(r == CUDA_SUCCESS, LR_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
-  return m;
-}
-
 template <int MODE, int NCOL, bool SPLITB = false, bool OUT64 = false>
 void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMap& mbl, ViewParams p, int tiles,
                  int sms, cudaStream_t s) {
