@@ -30,6 +30,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -236,6 +238,234 @@ def dual_sketch_cases(a, hbm, bf16_pk, reps=10):
     return out
 
 
+# ------------------------------------------------ the other workloads
+def _timed(fn, reps):
+    """Median of `reps` CUDA-event timings of fn() (ms), after one warm-up call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _tf32_peak(bf16_pk):
+    """TF32 dense peak: the measured BF16 peak times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    return bf16_pk * 1.1 / 2.25
+
+
+def workload_c2(dev, hbm, bf16_pk, reps=5):
+    """Single pass (Alg. 7) on A = U_256 diag(10^(-j/25)) V_256^T + 1e-4 N(0,1),
+    20000 x 10000 FP32, k = 50, Omega 10000 x 120, Psi 20000 x 240: the dual
+    sketch (FP32 form: three TF32 products per product, tensor-bound) and the
+    whole factorisation."""
+    import torch
+
+    from paper_1804_07531_gb300 import api, synth
+    from paper_1804_07531_gb300._binding import Handle
+    cfg = synth.CONFIGS["single_pass_20000x10000"]
+    m, n, r, k = cfg["m"], cfg["n"], cfg["rank"], cfg["k"]
+    u = synth.haar_torch(m, r, cfg["seed_u"], device=dev)
+    v = synth.haar_torch(n, r, cfg["seed_v"], device=dev)
+    sig = torch.tensor(synth.sigma_config("exp25", r), dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(cfg["seed_noise"])
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    a = (u * sig) @ v.t() + cfg["noise"] * torch.randn(m, n, generator=gen, device=dev)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del u, v
+    om = torch.randn(n, cfg["ell1"], generator=gen, device=dev)
+    ps = torch.randn(m, cfg["ell2"], generator=gen, device=dev)
+    h = Handle.get(dev)
+    ms_sketch = _timed(lambda: api.sketch(a, om, ps), reps)
+    h.set_trace(True)
+    h.trace_read("view_range", reset=True)
+    api.sketch(a, om, ps)
+    torch.cuda.synchronize()
+    r_ms, _ = h.trace_read("view_range")
+    c_ms, _ = h.trace_read("view_corange", reset=True)
+    h.set_trace(False)
+    ms_fact = _timed(lambda: api.single_pass(a, k, om, ps), reps)
+    st = api.device_status(dev.index or 0)
+    flops = 3 * 2.0 * m * n * (cfg["ell1"] + cfg["ell2"])
+    k_ms = r_ms + c_ms
+    a_bytes = m * n * 4
+    return {
+        "workload": "single_pass_f32_20000x10000_k50_l120_240", "status": st,
+        "sketch_ms_call": round(ms_sketch, 4), "sketch_ms_kernels": round(k_ms, 4),
+        "sketch_a_gbs": round(a_bytes / (k_ms * 1e-3) / 1e9, 1),
+        "roofline": {"bound": "tensor", "dtype": "tf32x3", "achieved": round(flops / (k_ms * 1e-3) / 1e12, 1),
+                     "peak": round(_tf32_peak(bf16_pk), 1), "unit": "TFLOP/s",
+                     "frac": round(flops / (k_ms * 1e-3) / 1e12 / _tf32_peak(bf16_pk), 4),
+                     "flops": flops, "note": "3 TF32 MMAs per product (hi*hi + hi*lo + lo*hi); peak = measured "
+                                             "BF16 burst x 1.1/2.25 (nominal TF32/BF16)"},
+        "factorisation_ms": round(ms_fact, 4),
+    }
+
+
+def workload_c3b(a, omega, reps=5):
+    """Block Krylov with the row-streamed variant of Sec. 7.3 (enhanced, v = 4)
+    on the workload's BF16 matrix: views 1-3 give A X and A^T (A X) each."""
+    from paper_1804_07531_gb300 import api
+    ms = _timed(lambda: api.block_krylov(a, K_RANK, P_OVER, VIEWS, omega, enhanced=True), reps)
+    a_bytes = a.numel() * a.element_size()
+    st = api.device_status(a.device.index or 0)
+    return {"workload": "block_krylov_enhanced_v4_bf16_65536x16384_k100_p20", "status": st,
+            "ms_per_factorisation": round(ms, 4),
+            "a_reads": 7, "paper_views": VIEWS,
+            "a_gbs_read": round(7 * a_bytes / (ms * 1e-3) / 1e9, 1),
+            "note": "views 1-3 each read A twice (A X, then A^T (A X) by a second pass), the last once"}
+
+
+def workload_c4(dev, reps=10):
+    """Differentiation: Alg. 2 (v = 4, k = 32, p = 8) forward and reverse on
+    A = U diag(sigma) V^T, 8192 x 4096 FP32, sigma_j = exp(-j/40) with a x0.1
+    gap after j = 32; loss = sum of the top-k singular values."""
+    import torch
+
+    from oracle import algorithms as Al
+    from paper_1804_07531_gb300 import api, synth
+    cfg = synth.CONFIGS["grad_8192x4096_v4"]
+    m, n, k, p, v = cfg["m"], cfg["n"], cfg["k"], cfg["p"], cfg["v"]
+    u = synth.haar_torch(m, n, cfg["seed_u"], device=dev)
+    vv = synth.haar_torch(n, n, cfg["seed_v"], device=dev)
+    sig = torch.tensor(synth.sigma_config("gap32", n), dtype=torch.float32, device=dev)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    a = ((u * sig) @ vv.t()).contiguous()
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del u, vv
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(cfg["seed_omega"])
+    om = torch.randn(n, k + p, generator=gen, device=dev)
+    ds = torch.ones(k, device=dev)
+    ms_f = _timed(lambda: api.subspace_iter(a, k, p, v, om), reps)
+    ms_b = _timed(lambda: api.subspace_iter_backward(a, k, p, v, om, ds), reps)
+    st = api.device_status(dev.index or 0)
+    a64 = a.double().cpu().numpy()
+    om64 = om.double().cpu().numpy()
+    t0 = time.perf_counter()
+    Al.gen_subspace_iteration(a64, om64, k, v)
+    t_orc = time.perf_counter() - t0
+    return {"workload": "grad_subspace_v4_f32_8192x4096_k32_p8", "status": st,
+            "forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),
+            "forward_plus_backward_ms": round(ms_f + ms_b, 4),
+            "cpu_oracle_forward_s": round(t_orc, 3), "cpu_oracle_cores": _threads()}
+
+
+def _host_matrix(m, n, r, seed, dev):
+    """Pinned host m x n FP32 A = U_r diag(1/j) V_r^T + 1e-5 N(0,1) (U, V Haar,
+    r = 1024 terms of the sigma_j = 1/j spectrum), built on the device in
+    4096-row blocks and copied out; None when the pinned allocation fails."""
+    import torch
+
+    from paper_1804_07531_gb300 import synth
+    try:
+        a_host = torch.empty(m, n, dtype=torch.float32).pin_memory()
+    except RuntimeError:
+        return None
+    u = synth.haar_torch(m, r, seed, device=dev)
+    v = synth.haar_torch(n, r, seed + 1, device=dev)
+    sig = 1.0 / torch.arange(1, r + 1, device=dev, dtype=torch.float32)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed + 2)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for i0 in range(0, m, 4096):
+        blk = (u[i0:i0 + 4096] * sig) @ v.t()
+        blk += 1e-5 * torch.randn(blk.shape, generator=gen, device=dev)
+        a_host[i0:i0 + 4096].copy_(blk)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del u, v
+    torch.cuda.synchronize()
+    return a_host
+
+
+def workload_c5(dev, sweep=True):
+    """Host-streamed single pass and Alg. 2 (A in pinned host memory, 4096-column
+    panels) at the largest of 262144 / 131072 / 65536 rows x 65536 columns that
+    can be pinned, against a plain pinned H2D copy measured in the same run
+    (the host link's roof); plus the v = 1..6 accuracy sweep against the FP64
+    oracle on a scaled matrix of the same family (8192 x 2048, k = 50,
+    ell1 = 100, ell2 = 200, ell = 100 for v >= 2)."""
+    import torch
+
+    from paper_1804_07531_gb300 import api
+    n, k, ell1, ell2, pc = 65536, 200, 400, 800, 4096
+    out = {"workload": "host_stream_f32_k200_l400_800_panels4096"}
+    a_host = None
+    for m in (262144, 131072, 65536):
+        a_host = _host_matrix(m, n, 1024, 51, dev)
+        if a_host is not None:
+            break
+    if a_host is None:
+        out["unavailable"] = "no pinned host allocation of 16 GiB or more"
+        return out
+    a_bytes = a_host.numel() * 4
+    out.update({"m": m, "n": n, "a_gib": round(a_bytes / 2 ** 30, 1)})
+    # the link: a plain pinned copy of up to 8 GiB of A
+    rows = min(m, 32768)
+    d = torch.empty(rows, n, device=dev)
+    d.copy_(a_host[:rows], non_blocking=True)
+    torch.cuda.synchronize()
+    t = _timed(lambda: d.copy_(a_host[:rows], non_blocking=True), 3)
+    link = rows * n * 4 / (t * 1e-3) / 1e9
+    del d
+    torch.cuda.empty_cache()
+    out["link_h2d_gbs"] = round(link, 1)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(53)
+    om = torch.randn(n, ell1, generator=gen, device=dev)
+    ps = torch.randn(m, ell2, generator=gen, device=dev)
+    for name, views, fn in (("single_pass_v1", 1, lambda: api.single_pass_host(a_host, k, om, ps, panel_cols=pc)),
+                            ("subspace_v2", 2,
+                             lambda: api.subspace_iter_host(a_host, k, ell1 - k, 2, om, panel_cols=pc))):
+        ms = _timed(fn, 1)
+        gbs = views * a_bytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": round(ms, 1), "a_gbs": round(gbs, 1), "frac_of_link": round(gbs / link, 3),
+                     "status": api.device_status(dev.index or 0)}
+    del a_host
+    if sweep:
+        out["accuracy_sweep"] = _c5_sweep(dev)
+    return out
+
+
+def _c5_sweep(dev):
+    import torch
+
+    from oracle import algorithms as Al
+    from paper_1804_07531_gb300 import api, synth
+    m, n, k, l1, l2 = 8192, 2048, 50, 100, 200
+    a64 = synth.usv(m, n, synth.sigma_config("inv", n), 61, 62) + 1e-5 * synth.gaussian(m, n, seed=63)
+    a32 = a64.astype(np.float32)
+    a = a32.astype(np.float64)
+    om = synth.gaussian(n, l1, seed=64).astype(np.float32)
+    ps = synth.gaussian(m, l2, seed=65).astype(np.float32)
+    ah = torch.tensor(a32).pin_memory()
+    tom, tps = torch.tensor(om, device=dev), torch.tensor(ps, device=dev)
+    best = float(np.sqrt(np.sum(np.linalg.svd(a, compute_uv=False)[k:] ** 2)))
+    rows = []
+    for v in range(1, 7):
+        if v == 1:
+            ug, sg, vg = api.single_pass_host(ah, k, tom, tps, panel_cols=512)
+            uo, so, vo = Al.single_pass(a, om.astype(np.float64), ps.astype(np.float64), k)
+        else:
+            ug, sg, vg = api.subspace_iter_host(ah, k, l1 - k, v, tom, panel_cols=512)
+            uo, so, vo = Al.gen_subspace_iteration(a, om.astype(np.float64), k, v)
+        e_g = Al.frob_error(a, ug.double().cpu().numpy(), sg.double().cpu().numpy(), vg.double().cpu().numpy())
+        e_o = Al.frob_error(a, uo, so, vo)
+        rows.append({"v": v, "rel_err_gpu": e_g / np.linalg.norm(a), "rel_err_oracle": e_o / np.linalg.norm(a),
+                     "gpu_vs_oracle": abs(e_g - e_o) / e_o, "err_over_optimal": e_g / best})
+    return {"shape": [m, n], "k": k, "ell1": l1, "ell2": l2, "panels": 512, "rows": rows}
+
+
 # --------------------------------------------------------- CPU baseline
 CPU_ROWS = 1024
 
@@ -336,9 +566,11 @@ def run_ours(args):
     total_bytes = _sum_over_ranks(dist, VIEWS * a_bytes * args.steps, dev)
     value = total_bytes / (ms_max * args.steps * 1e-3) / 1e9
 
-    # ---- the one-read dual sketch on the same matrix
+    # ---- the one-read dual sketch, and the enhanced block Krylov, on the same matrix
     hbm0, bf16_pk0, _ = _peaks()
-    dual = dual_sketch_cases(a, hbm0, bf16_pk0) if rank == 0 else None
+    extra = rank == 0 and not args.no_extra
+    dual = dual_sketch_cases(a, hbm0, bf16_pk0) if extra else None
+    workloads = {"c3b": workload_c3b(a, omega)} if extra else {}
 
     # ---- accuracy of the BF16 form, and the FP32 form at equal error
     e_bf16 = recon_error(a, u, s, v)
@@ -361,30 +593,23 @@ def run_ours(args):
     del a32
     torch.cuda.empty_cache()
 
-    # ---- end to end: host-resident A and Omega, copies inside the timed region
+    # ---- end to end through the C ABI with host buffers: lr_block_krylov_host
+    # copies A and Omega from pinned host memory into the device workspace,
+    # factorises, and copies U, S, V back into pinned host buffers, every step
     a_host = a.cpu().pin_memory()
-    om_host = omega.cpu().pin_memory()
+    om_host = torch.empty(K_RANK + P_OVER, N, dtype=torch.float32).pin_memory().t()
+    om_host.copy_(omega)
     del a
     torch.cuda.empty_cache()
-    a_dev = torch.empty(a_host.shape, dtype=a_host.dtype, device=dev)
-    om_dev = torch.empty(om_host.shape, dtype=om_host.dtype, device=dev)
     e2e_steps = max(1, min(args.steps, 5))
-
-    # the results land in pinned host buffers (allocated once, as a caller
-    # streaming many factorisations would); every step waits for its copy
-    outs_host = None
+    outs_host = (torch.empty(K_RANK, M, dtype=torch.float32).pin_memory().t(),
+                 torch.empty(K_RANK, dtype=torch.float32).pin_memory(),
+                 torch.empty(K_RANK, N, dtype=torch.float32).pin_memory().t())
 
     def e2e_step():
-        nonlocal outs_host
-        a_dev.copy_(a_host, non_blocking=True)
-        om_dev.copy_(om_host, non_blocking=True)
-        res = api.block_krylov(a_dev, K_RANK, P_OVER, VIEWS, om_dev)
-        if outs_host is None:
-            outs_host = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in res]
-        for h, t in zip(outs_host, res):
-            h.copy_(t, non_blocking=True)
+        res = api.block_krylov_host(a_host, K_RANK, P_OVER, VIEWS, om_host, out=outs_host)
         torch.cuda.current_stream().synchronize()
-        return outs_host
+        return res
 
     e2e_step()
     torch.cuda.synchronize()
@@ -398,6 +623,12 @@ def run_ours(args):
     e2e_val = _sum_over_ranks(dist, VIEWS * a_bytes, dev) / t_e2e / 1e9
     h2d = a_host.numel() * a_host.element_size() + om_host.numel() * 4
     d2h = sum(t.numel() * t.element_size() for t in out)
+    e_e2e = float(np.abs(out[1].numpy() - s.cpu().numpy()).max() / float(s[0]))
+    del a_host
+    if extra:
+        workloads["c2"] = workload_c2(dev, hbm0, bf16_pk0)
+        workloads["c4"] = workload_c4(dev)
+        workloads["c5"] = workload_c5(dev)
 
     if rank != 0:
         return
@@ -443,8 +674,11 @@ def run_ours(args):
             "bf16_over_fp32_error": e_bf16 / e_fp32, "bf16_speedup": ms_fp32 / ms_max,
         },
         "dual_sketch": dual,
+        "workloads": workloads,
         "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t_e2e * 1e3, 3)},
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t_e2e * 1e3, 3),
+                "call": "lr_block_krylov_host (pinned host A, Omega in; U, S, V out)",
+                "sigma_vs_device_run": e_e2e},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -618,10 +852,12 @@ def run_host_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the dual-sketch comparison and the other workloads (C2, C3b, C4, C5)")
     ap.add_argument("--kernel-case", default=None,
                     choices=["view_range", "view_corange", "view_range_f32", "view_corange_f32", "dual_bf16",
                              "dual_f32", "chained_bf16", "chained_f32", "orth", "block_krylov", "host_stream"],

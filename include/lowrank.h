@@ -198,6 +198,20 @@ lr_status lr_subspace_iter_host(lr_handle handle, const lr_mat* A_host, int64_t 
                                 const lr_mat* Omega, lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts,
                                 void* stream);
 
+/* Alg. 9 (as lr_block_krylov) end to end from host buffers: A_host (F32 or
+ * BF16 row-major, page-locked) and Omega_host (F32 column-major n x (k+p))
+ * are copied once into the device workspace on `stream`, the factorisation
+ * runs on the device (all v views read the device copy), and U_host,
+ * S_host, V_host (F32; U m x k and V n x k column-major, page-locked) receive
+ * the results by device-to-host copies queued on `stream`: they are valid
+ * once `stream` has finished.  The workspace needs lr_workspace_size(m, n,
+ * k + p, 0, v) plus the staging of A (m * ld * element size), Omega, U, S
+ * and V, each rounded up to 256 bytes.  Errors as lr_block_krylov, and
+ * LR_ERR_INVALID_ARG when a host buffer is not page-locked. */
+lr_status lr_block_krylov_host(lr_handle handle, const lr_mat* A_host, int k, int p, int v,
+                               const lr_mat* Omega_host, lr_mat* U_host, lr_mat* S_host, lr_mat* V_host,
+                               const lr_opts* opts, void* stream);
+
 /* Reverse pass of lr_subspace_iter for the loss L = sum_i dS_i sigma_i
  * (dS: k weights, F32): writes dA = dL/dA (m x n, F32 row-major, same shape
  * as A, overwritten).  The forward views are recomputed, not stored.  A must

@@ -30,7 +30,7 @@ EXPORTS = [
     "lr_create", "lr_destroy", "lr_status_string", "lr_last_error", "lr_workspace_size",
     "lr_set_workspace", "lr_get_status", "lr_sketch", "lr_sketch_chained", "lr_orth",
     "lr_subspace_iter", "lr_single_pass", "lr_block_krylov", "lr_rowwise_single_pass",
-    "lr_single_pass_host", "lr_subspace_iter_host", "lr_subspace_iter_backward", "lr_set_trace", "lr_trace_read",
+    "lr_single_pass_host", "lr_subspace_iter_host", "lr_block_krylov_host", "lr_subspace_iter_backward", "lr_set_trace", "lr_trace_read",
     "lr_kernel_launches", "lr_sketch_range_static", "lr_sketch_range_static_status", "lr_selftest_bounded_wait",
 ]
 TRACE_KINDS = {"view_range": 0, "view_corange": 1, "orth": 2, "core_svd": 3, "view_dual": 4}
@@ -88,6 +88,7 @@ def lib():
             L.lr_rowwise_single_pass.argtypes = [P, M, I, M, M, M, M, O, P]
             L.lr_single_pass_host.argtypes = [P, M, I64, I, M, M, M, M, M, O, P]
             L.lr_subspace_iter_host.argtypes = [P, M, I64, I, I, I, M, M, M, M, O, P]
+            L.lr_block_krylov_host.argtypes = [P, M, I, I, I, M, M, M, M, O, P]
             L.lr_subspace_iter_backward.argtypes = [P, M, I, I, I, M, M, M, O, P]
             L.lr_set_trace.argtypes = [P, I]
             L.lr_trace_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I]

@@ -17,7 +17,8 @@ from ._binding import (Handle, LowrankError, LrMat, _opts, _stream, col_major, e
 
 __all__ = [
     "sketch", "sketch_chained", "orth", "subspace_iter", "single_pass", "block_krylov",
-    "rowwise_single_pass", "subspace_iter_backward", "single_pass_host", "subspace_iter_host", "device_status",
+    "rowwise_single_pass", "subspace_iter_backward", "single_pass_host", "subspace_iter_host", "block_krylov_host",
+    "device_status",
     "LowrankError",
 ]
 
@@ -241,4 +242,40 @@ def subspace_iter_host(a_host, k, p, v, omega, panel_cols=4096, device=None, str
     o = _opts()
     _call(h, lib().lr_subspace_iter_host, _p(mh), pc, k, p, v, _p(mats[0]), _p(mats[1]), _p(mats[2]),
           _p(mats[3]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+def block_krylov_host(a_host, k, p, v, omega_host, out=None, enhanced=False, split_last=False, device=None,
+                      stream=None):
+    """Alg. 9 end to end from pinned host buffers (lr_block_krylov_host): A
+    and Omega are copied once into the device workspace, all views read the
+    device copy, and U, S, V come back into pinned host tensors (`out`, or new
+    ones).  The results are valid after the stream synchronises."""
+    if a_host.is_cuda or a_host.dtype not in (torch.float32, torch.bfloat16) or a_host.stride(1) != 1:
+        raise ValueError("a_host must be a row-major float32 or bfloat16 CPU tensor")
+    if not a_host.is_pinned():
+        raise ValueError("a_host must be in pinned memory (tensor.pin_memory())")
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    m, n = a_host.shape
+    ell = k + p
+    om = omega_host
+    if om.is_cuda or om.dtype != torch.float32 or om.stride(0) != 1 or om.stride(1) < n or not om.is_pinned():
+        om = torch.empty(ell, n, dtype=torch.float32).pin_memory().t()   # pinned, column-major
+        om.copy_(omega_host)
+    if out is None:
+        u = torch.empty(k, m, dtype=torch.float32).pin_memory().t()
+        s = torch.empty(k, dtype=torch.float32).pin_memory()
+        vv = torch.empty(k, n, dtype=torch.float32).pin_memory().t()
+    else:
+        u, s, vv = out
+    h = Handle.get(dev)
+    esz = a_host.element_size()
+    staging = sum((b + 255) // 256 * 256 for b in (m * a_host.stride(0) * esz, n * ell * 4, m * k * 4, n * k * 4, k * 4))
+    h.reserve(m, n, ell, 0, v, extra=staging + 1024)
+    mh = LrMat(a_host.data_ptr(), m, n, a_host.stride(0), 1 if a_host.dtype == torch.bfloat16 else 0, 0)
+    mats = [mat_thin(om), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts(enhanced=enhanced, split_last=split_last)
+    with torch.cuda.device(dev):
+        _call(h, lib().lr_block_krylov_host, _p(mh), k, p, v, _p(mats[0]), _p(mats[1]), _p(mats[2]), _p(mats[3]),
+              ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return u, s, vv

@@ -1337,6 +1337,53 @@ lr_status lr_subspace_iter_host(lr_handle h, const lr_mat* A_host, int64_t panel
   });
 }
 
+lr_status lr_block_krylov_host(lr_handle h, const lr_mat* A_host, int k, int p, int v, const lr_mat* Omega_host,
+                               lr_mat* U_host, lr_mat* S_host, lr_mat* V_host, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    LR_REQUIRE(A_host && A_host->data, LR_ERR_INVALID_ARG, "A_host is NULL");
+    LR_REQUIRE(A_host->dtype == LR_F32 || A_host->dtype == LR_BF16, LR_ERR_DTYPE, "A_host must be F32 or BF16");
+    LR_REQUIRE(A_host->col_major == 0, LR_ERR_DTYPE, "A_host must be row-major");
+    LR_REQUIRE(A_host->rows >= 1 && A_host->cols >= 1 && A_host->ld >= A_host->cols, LR_ERR_SHAPE, "bad A_host");
+    auto pinned = [](const void* ptr) {
+      cudaPointerAttributes pa{};
+      return ptr && cudaPointerGetAttributes(&pa, ptr) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    };
+    AMat a;  // shapes; the data moves to the workspace below
+    a.m = A_host->rows;
+    a.n = A_host->cols;
+    a.ld = A_host->ld;
+    a.bf16 = A_host->dtype == LR_BF16;
+    LR_REQUIRE((A_host->ld * int64_t(a.elem())) % 16 == 0, LR_ERR_ALIGNMENT, "A row stride not a multiple of 16 bytes");
+    check_kpv(a, k, p, v, 2);
+    const int ell = k + p;
+    const int nb = (v % 2 == 0) ? v / 2 : (v - 1) / 2;
+    LR_REQUIRE(int64_t(nb) * ell <= std::min(a.m, a.n), LR_ERR_INVALID_ARG, "Krylov basis wider than A");
+    Mat om_h = check_thin(Omega_host, a.n, ell, "Omega_host");
+    Outs oh = check_outs(a, k, U_host, S_host, V_host);
+    LR_REQUIRE(pinned(A_host->data) && pinned(om_h.p) && pinned(oh.U.p) && pinned(oh.V.p) && pinned(oh.S),
+               LR_ERR_INVALID_ARG, "host buffers must be pinned (page-locked)");
+    Ctx c = make_ctx(h, opts, stream);
+    ArenaScope sc(c.ar);
+    char* a_dev = c.ar.take<char>(size_t(a.m) * size_t(a.ld) * a.elem());
+    Mat om{c.ar.take<float>(size_t(a.n) * ell), a.n, ell, a.n};
+    Outs o;
+    o.U = Mat{c.ar.take<float>(size_t(a.m) * k), a.m, k, a.m};
+    o.V = Mat{c.ar.take<float>(size_t(a.n) * k), a.n, k, a.n};
+    o.S = c.ar.take<float>(size_t(k));
+    LR_CHECK_CUDA(cudaMemcpyAsync(a_dev, A_host->data, size_t(a.m) * size_t(a.ld) * a.elem(), cudaMemcpyHostToDevice,
+                                  c.s));
+    LR_CHECK_CUDA(cudaMemcpy2DAsync(om.p, size_t(om.ld) * 4, om_h.p, size_t(om_h.ld) * 4, size_t(a.n) * 4, size_t(ell),
+                                    cudaMemcpyHostToDevice, c.s));
+    a.p = a_dev;
+    run_krylov(c, a, k, ell, v, om, o);
+    LR_CHECK_CUDA(cudaMemcpy2DAsync(oh.U.p, size_t(oh.U.ld) * 4, o.U.p, size_t(o.U.ld) * 4, size_t(a.m) * 4, size_t(k),
+                                    cudaMemcpyDeviceToHost, c.s));
+    LR_CHECK_CUDA(cudaMemcpy2DAsync(oh.V.p, size_t(oh.V.ld) * 4, o.V.p, size_t(o.V.ld) * 4, size_t(a.n) * 4, size_t(k),
+                                    cudaMemcpyDeviceToHost, c.s));
+    LR_CHECK_CUDA(cudaMemcpyAsync(oh.S, o.S, sizeof(float) * k, cudaMemcpyDeviceToHost, c.s));
+  });
+}
+
 lr_status lr_subspace_iter_backward(lr_handle h, const lr_mat* A, int k, int p, int v, const lr_mat* Omega,
                                     const lr_mat* dS, lr_mat* dA, const lr_opts* opts, void* stream) {
   return guarded(h, [&] {

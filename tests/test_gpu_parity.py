@@ -363,3 +363,24 @@ def test_bounded_wait_times_out_and_reports():
     assert_status_ok()
     uo, so, vo = Al.gen_subspace_iteration(a64.astype(np.float32).astype(np.float64), om.astype(np.float64), k, 2)
     check_tsvd(a64.astype(np.float32).astype(np.float64), u, s, vv, uo, so, vo)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_block_krylov_from_host_buffers_matches_device_run(c1, dtype):
+    """lr_block_krylov_host: A and Omega in pinned host memory, U, S, V back
+    into pinned host buffers; the same factorisation as the device-resident
+    call (and, for an F32 A, the oracle's)."""
+    cfg, a32, om = c1
+    k, p, v = cfg["k"], cfg["p"], 4
+    a_t = torch.tensor(a32) if dtype == "f32" else torch.tensor(a32).bfloat16()
+    ah = a_t.pin_memory()
+    u, s, vv = api().block_krylov_host(ah, k, p, v, torch.tensor(om))
+    torch.cuda.synchronize()
+    assert not u.is_cuda and not s.is_cuda and not vv.is_cuda
+    assert_status_ok()
+    ud, sd, vd = api().block_krylov(a_t.to(DEV), k, p, v, t32(om))
+    assert np.abs(s.double().numpy() - f64(sd)).max() / f64(sd)[0] < 1e-5
+    if dtype == "f32":
+        a64 = a32.astype(np.float64)
+        uo, so, vo = Al.block_krylov(a64, om.astype(np.float64), k, v)
+        print(check_tsvd(a64, u, s, vv, uo, so, vo))
