@@ -360,15 +360,17 @@ def workload_c4(dev, reps=10):
             "cpu_oracle_forward_s": round(t_orc, 3), "cpu_oracle_cores": _threads()}
 
 
-def _host_matrix(m, n, r, seed, dev):
-    """Pinned host m x n FP32 A = U_r diag(1/j) V_r^T + 1e-5 N(0,1) (U, V Haar,
-    r = 1024 terms of the sigma_j = 1/j spectrum), built on the device in
-    4096-row blocks and copied out; None when the pinned allocation fails."""
+def _host_matrix(m, n, r, seed, dev, pc):
+    """Pinned host A = U_r diag(1/j) V_r^T + 1e-5 N(0,1), m x n FP32 (U, V Haar,
+    r = 1024 terms of the sigma_j = 1/j spectrum), stored as n / pc contiguous
+    column panels of pc columns (a (n / pc, m, pc) tensor), built on the
+    device in 4096-row blocks and copied out; None when the pinned allocation
+    fails."""
     import torch
 
     from paper_1804_07531_gb300 import synth
     try:
-        a_host = torch.empty(m, n, dtype=torch.float32).pin_memory()
+        a_host = torch.empty(n // pc, m, pc, dtype=torch.float32).pin_memory()
     except RuntimeError:
         return None
     u = synth.haar_torch(m, r, seed, device=dev)
@@ -381,7 +383,8 @@ def _host_matrix(m, n, r, seed, dev):
     for i0 in range(0, m, 4096):
         blk = (u[i0:i0 + 4096] * sig) @ v.t()
         blk += 1e-5 * torch.randn(blk.shape, generator=gen, device=dev)
-        a_host[i0:i0 + 4096].copy_(blk)
+        for p in range(n // pc):
+            a_host[p, i0:i0 + 4096].copy_(blk[:, p * pc:(p + 1) * pc])
     torch.backends.cuda.matmul.allow_tf32 = prev
     del u, v
     torch.cuda.synchronize()
@@ -389,10 +392,10 @@ def _host_matrix(m, n, r, seed, dev):
 
 
 def workload_c5(dev, sweep=True):
-    """Host-streamed single pass and Alg. 2 (A in pinned host memory, 4096-column
-    panels) at the largest of 262144 / 131072 / 65536 rows x 65536 columns that
-    can be pinned, against a plain pinned H2D copy measured in the same run
-    (the host link's roof); plus the v = 1..6 accuracy sweep against the FP64
+    """Host-streamed single pass and Alg. 2 (A in pinned host memory as 4096-column
+    panels, each stored contiguously) at the largest of 262144 / 131072 / 65536
+    rows x 65536 columns that can be pinned, against a plain pinned H2D copy of
+    one panel measured in the same run (the host link's roof); plus the v = 1..6 accuracy sweep against the FP64
     oracle on a scaled matrix of the same family (8192 x 2048, k = 50,
     ell1 = 100, ell2 = 200, ell = 100 for v >= 2)."""
     import torch
@@ -402,21 +405,29 @@ def workload_c5(dev, sweep=True):
     out = {"workload": "host_stream_f32_k200_l400_800_panels4096"}
     a_host = None
     for m in (262144, 131072, 65536):
-        a_host = _host_matrix(m, n, 1024, 51, dev)
+        a_host = _host_matrix(m, n, 1024, 51, dev, pc)
         if a_host is not None:
             break
     if a_host is None:
         out["unavailable"] = "no pinned host allocation of 16 GiB or more"
         return out
     a_bytes = a_host.numel() * 4
-    out.update({"m": m, "n": n, "a_gib": round(a_bytes / 2 ** 30, 1)})
-    # the link: a plain pinned copy of up to 8 GiB of A
-    rows = min(m, 32768)
-    d = torch.empty(rows, n, device=dev)
-    d.copy_(a_host[:rows], non_blocking=True)
+    out.update({"m": m, "n": n, "a_gib": round(a_bytes / 2 ** 30, 1), "layout": "contiguous 4096-column panels"})
+    # the link: plain pinned copies of every panel (m x pc each, contiguous) into
+    # one device buffer, the host-to-device traffic of one view without the
+    # sketches; a single panel alone copies faster than the whole buffer does
+    d = torch.empty(m, pc, device=dev)
+    d.copy_(a_host[0], non_blocking=True)
     torch.cuda.synchronize()
-    t = _timed(lambda: d.copy_(a_host[:rows], non_blocking=True), 3)
-    link = rows * n * 4 / (t * 1e-3) / 1e9
+
+    def copy_all():
+        for i in range(a_host.shape[0]):
+            d.copy_(a_host[i], non_blocking=True)
+
+    t = _timed(copy_all, 1)
+    link = a_bytes / (t * 1e-3) / 1e9
+    t1 = _timed(lambda: d.copy_(a_host[0], non_blocking=True), 3)
+    out["one_panel_h2d_gbs"] = round(m * pc * 4 / (t1 * 1e-3) / 1e9, 1)
     del d
     torch.cuda.empty_cache()
     out["link_h2d_gbs"] = round(link, 1)
@@ -424,9 +435,8 @@ def workload_c5(dev, sweep=True):
     gen.manual_seed(53)
     om = torch.randn(n, ell1, generator=gen, device=dev)
     ps = torch.randn(m, ell2, generator=gen, device=dev)
-    for name, views, fn in (("single_pass_v1", 1, lambda: api.single_pass_host(a_host, k, om, ps, panel_cols=pc)),
-                            ("subspace_v2", 2,
-                             lambda: api.subspace_iter_host(a_host, k, ell1 - k, 2, om, panel_cols=pc))):
+    for name, views, fn in (("single_pass_v1", 1, lambda: api.single_pass_host(a_host, k, om, ps)),
+                            ("subspace_v2", 2, lambda: api.subspace_iter_host(a_host, k, ell1 - k, 2, om))):
         ms = _timed(fn, 1)
         gbs = views * a_bytes / (ms * 1e-3) / 1e9
         out[name] = {"ms": round(ms, 1), "a_gbs": round(gbs, 1), "frac_of_link": round(gbs / link, 3),

@@ -94,7 +94,13 @@ typedef struct {
                                -2 = the fused kernel whenever ell1 <= 128, ell2 <= 256;
                                -1 = two full passes; > 0 = L2 bands of that many MiB of
                                A, each read by the two products back to back */
-  int32_t reserved[3];
+  int32_t host_panels;      /* host-streamed calls: 0 = A_host row-major m x n (ld); 1 = A_host
+                               stored as ceil(n / panel_cols) column panels, panel i at
+                               element offset i * m * panel_cols, each m x panel_cols
+                               row-major (ld = panel_cols; the last panel's columns past n
+                               unused): every panel then crosses the host link as one
+                               contiguous copy.  panel_cols must be a multiple of 4 */
+  int32_t reserved[2];
 } lr_opts;
 
 typedef struct lr_handle_s* lr_handle;
@@ -178,7 +184,8 @@ lr_status lr_rowwise_single_pass(lr_handle handle, const lr_mat* A, int k, const
  * panels): A_host is F32 row-major in pinned host memory; it is copied to the
  * device in panels of panel_cols columns through two device panel buffers
  * (carved from the workspace) on a copy stream overlapped with the sketches,
- * so A crosses the host link once.  The workspace needs
+ * so A crosses the host link once.  With opts->host_panels = 1 A_host is
+ * stored panel by panel (see lr_opts) and each panel is one contiguous copy.  The workspace needs
  * lr_workspace_size(m, n, ell1, ell2, 1) plus 2 * m * round4(panel_cols) * 4
  * bytes.  Errors: LR_ERR_INVALID_ARG also when A_host is not page-locked.
  * Otherwise as lr_single_pass. */

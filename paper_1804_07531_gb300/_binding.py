@@ -44,7 +44,7 @@ class LrMat(ctypes.Structure):
 class LrOpts(ctypes.Structure):
     _fields_ = [("l_c", ctypes.c_int32), ("enhanced", ctypes.c_int32), ("split_last", ctypes.c_int32),
                 ("shifted_fallback", ctypes.c_int32), ("band_mb", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("host_panels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class LowrankError(RuntimeError):
@@ -204,9 +204,10 @@ def _stream(stream=None) -> int:
     return stream.cuda_stream
 
 
-def _opts(l_c=-1, enhanced=False, split_last=False, shifted_fallback=False, band_mb=0) -> LrOpts:
+def _opts(l_c=-1, enhanced=False, split_last=False, shifted_fallback=False, band_mb=0, host_panels=False) -> LrOpts:
     o = LrOpts()
     o.band_mb = int(band_mb)
+    o.host_panels = int(bool(host_panels))
     o.l_c = -1 if l_c is None else -2 if l_c == "minvar" else int(l_c)
     o.enhanced = int(bool(enhanced))
     o.split_last = int(bool(split_last))

@@ -191,55 +191,67 @@ def subspace_iter_backward(a, k, p, v, omega, ds, stream=None):
     return da
 
 
-def single_pass_host(a_host, k, omega, psi, panel_cols=4096, l_c=None, device=None, stream=None):
-    """Alg. 7 on a pinned host A (float32, row-major), streamed in column panels.
-
-    A crosses the host link once: panels are copied through two device
-    buffers (2 * m * panel_cols floats of workspace) while the previous panel
-    is sketched.  omega / psi may live on the host or the device.
-    """
-    if a_host.is_cuda or a_host.dtype != torch.float32 or a_host.stride(1) != 1:
+def _host_a(a_host, panel_cols, n):
+    """(LrMat, m, n, panel width, panel layout?) for a pinned host A: a 2-D
+    row-major m x n tensor, or a 3-D (panels, m, panel_cols) tensor holding
+    contiguous column panels (the last one's columns past n unused)."""
+    if a_host.is_cuda or a_host.dtype != torch.float32 or not a_host.is_contiguous() and a_host.stride(-1) != 1:
         raise ValueError("a_host must be a row-major float32 CPU tensor")
     if not a_host.is_pinned():
         raise ValueError("a_host must be in pinned memory (tensor.pin_memory())")
+    if a_host.dim() == 3:
+        if not a_host.is_contiguous():
+            raise ValueError("a panel-stored A must be contiguous")
+        npan, m, pc = a_host.shape
+        n = npan * pc if n is None else int(n)
+        if not (npan - 1) * pc < n <= npan * pc:
+            raise ValueError("n does not match the number of panels")
+        return LrMat(a_host.data_ptr(), m, n, pc, 0, 0), m, n, pc, True
+    m, n = a_host.shape
+    return LrMat(a_host.data_ptr(), m, n, a_host.stride(0), 0, 0), m, n, min(int(panel_cols), n), False
+
+
+def single_pass_host(a_host, k, omega, psi, panel_cols=4096, l_c=None, n=None, device=None, stream=None):
+    """Alg. 7 on a pinned host A (float32), streamed in column panels.
+
+    A crosses the host link once: panels are copied through two device
+    buffers (2 * m * panel_cols floats of workspace) while the previous panel
+    is sketched.  a_host is row-major m x n, or a (panels, m, panel_cols)
+    tensor of contiguous column panels (each panel then one contiguous copy;
+    n gives the true column count).  omega / psi may live on the host or the
+    device.
+    """
+    mh, m, n, pc, panels = _host_a(a_host, panel_cols, n)
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     omega = col_major(omega.to(device=dev, dtype=torch.float32))
     psi = col_major(psi.to(device=dev, dtype=torch.float32))
     h = Handle.get(dev)
-    m, n = a_host.shape
-    pc = min(int(panel_cols), n)
     h.reserve(m, n, omega.shape[1], psi.shape[1], 1, extra=2 * m * ((pc + 3) // 4 * 4) * 4 + 1024)
     u = empty_cm(m, k, dev)
     s = torch.empty(k, dtype=torch.float32, device=dev)
     vv = empty_cm(n, k, dev)
-    mh = LrMat(a_host.data_ptr(), m, n, a_host.stride(0), 0, 0)
     mats = [mat_thin(omega), mat_thin(psi), mat_thin(u), mat_thin(s), mat_thin(vv)]
-    o = _opts(l_c=l_c)
+    o = _opts(l_c=l_c, host_panels=panels)
     _call(h, lib().lr_single_pass_host, _p(mh), pc, k, _p(mats[0]), _p(mats[1]), _p(mats[2]), _p(mats[3]),
           _p(mats[4]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return u, s, vv
 
 
-def subspace_iter_host(a_host, k, p, v, omega, panel_cols=4096, device=None, stream=None):
-    """Alg. 2 on a pinned host A (float32, row-major): every view streams A in
-    column panels through two device buffers (2 * m * panel_cols floats of
-    workspace) while the previous panel is multiplied."""
-    if a_host.is_cuda or a_host.dtype != torch.float32 or a_host.stride(1) != 1:
-        raise ValueError("a_host must be a row-major float32 CPU tensor")
-    if not a_host.is_pinned():
-        raise ValueError("a_host must be in pinned memory (tensor.pin_memory())")
+def subspace_iter_host(a_host, k, p, v, omega, panel_cols=4096, n=None, device=None, stream=None):
+    """Alg. 2 on a pinned host A (float32; layouts as in single_pass_host):
+    every view streams A in column panels through two device buffers
+    (2 * m * panel_cols floats of workspace) while the previous panel is
+    multiplied."""
+    mh, m, n, pc, panels = _host_a(a_host, panel_cols, n)
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     omega = col_major(omega.to(device=dev, dtype=torch.float32))
     h = Handle.get(dev)
-    m, n = a_host.shape
-    pc = min(int(panel_cols), n)
     h.reserve(m, n, k + p, 0, v, extra=2 * m * ((pc + 3) // 4 * 4) * 4 + 1024)
     u = empty_cm(m, k, dev)
     s = torch.empty(k, dtype=torch.float32, device=dev)
     vv = empty_cm(n, k, dev)
-    mh = LrMat(a_host.data_ptr(), m, n, a_host.stride(0), 0, 0)
     mats = [mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
-    o = _opts()
+    o = _opts(host_panels=panels)
     _call(h, lib().lr_subspace_iter_host, _p(mh), pc, k, p, v, _p(mats[0]), _p(mats[1]), _p(mats[2]),
           _p(mats[3]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return u, s, vv

@@ -902,6 +902,7 @@ void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const M
 struct HostA {
   const float* p = nullptr;
   int64_t m = 0, n = 0, ld = 0;
+  bool panels = false;  // stored as contiguous column panels (lr_opts.host_panels)
 };
 
 // Views of a pinned host A streamed in column panels: Y = A X (X: n x ell,
@@ -940,8 +941,13 @@ void host_views(Ctx& c, const HostA& H, int64_t pc, const Mat* X, Mat* Y, const 
     const int b = i & 1;
     const int64_t c0 = int64_t(i) * pc, w = std::min(pc, H.n - c0);
     LR_CHECK_CUDA(cudaStreamWaitEvent(h->copy_stream, h->consumed[b], 0));
-    LR_CHECK_CUDA(cudaMemcpy2DAsync(buf[b], size_t(ldp) * sizeof(float), H.p + c0, size_t(H.ld) * sizeof(float),
-                                    size_t(w) * sizeof(float), size_t(H.m), cudaMemcpyHostToDevice, h->copy_stream));
+    if (H.panels)  // panel i is one contiguous m x pc block
+      LR_CHECK_CUDA(cudaMemcpyAsync(buf[b], H.p + int64_t(i) * H.m * pc, size_t(H.m) * size_t(pc) * sizeof(float),
+                                    cudaMemcpyHostToDevice, h->copy_stream));
+    else
+      LR_CHECK_CUDA(cudaMemcpy2DAsync(buf[b], size_t(ldp) * sizeof(float), H.p + c0, size_t(H.ld) * sizeof(float),
+                                      size_t(w) * sizeof(float), size_t(H.m), cudaMemcpyHostToDevice,
+                                      h->copy_stream));
     LR_CHECK_CUDA(cudaEventRecord(h->copied[b], h->copy_stream));
     LR_CHECK_CUDA(cudaStreamWaitEvent(c.s, h->copied[b], 0));
     AMat P;
@@ -1283,7 +1289,9 @@ lr_status lr_single_pass_host(lr_handle h, const lr_mat* A_host, int64_t panel_c
   return guarded(h, [&] {
     LR_REQUIRE(A_host && A_host->data, LR_ERR_INVALID_ARG, "A_host is NULL");
     LR_REQUIRE(A_host->dtype == LR_F32 && A_host->col_major == 0, LR_ERR_DTYPE, "A_host must be F32 row-major");
-    LR_REQUIRE(A_host->rows >= 1 && A_host->cols >= 1 && A_host->ld >= A_host->cols, LR_ERR_SHAPE, "bad A_host");
+    LR_REQUIRE(A_host->rows >= 1 && A_host->cols >= 1 &&
+                   (A_host->ld >= A_host->cols || (opts && opts->host_panels)),
+               LR_ERR_SHAPE, "bad A_host");
     LR_REQUIRE(panel_cols >= 1, LR_ERR_INVALID_ARG, "panel_cols must be positive");
     cudaPointerAttributes pa{};
     LR_CHECK_CUDA(cudaPointerGetAttributes(&pa, A_host->data));
@@ -1300,8 +1308,11 @@ lr_status lr_single_pass_host(lr_handle h, const lr_mat* A_host, int64_t panel_c
                "need ell2 >= ell1 > k and ell2 <= min(m, n)");
     Outs o = check_outs(a, k, U, S, V);
     Ctx c = make_ctx(h, opts, stream);
-    HostA H{static_cast<const float*>(A_host->data), a.m, a.n, A_host->ld};
-    const int64_t pc = std::min<int64_t>(panel_cols, a.n);
+    const bool panels = opts && opts->host_panels;
+    LR_REQUIRE(!panels || (panel_cols % 4 == 0 && A_host->ld == panel_cols), LR_ERR_SHAPE,
+               "panel layout: panel_cols must be a multiple of 4 and A_host->ld == panel_cols");
+    HostA H{static_cast<const float*>(A_host->data), a.m, a.n, A_host->ld, panels};
+    const int64_t pc = panels ? panel_cols : std::min<int64_t>(panel_cols, a.n);
     run_single_pass(c, a, k, opts ? opts->l_c : -1, om, ps, o,
                     [&](Ctx& cc, Mat Y, Mat Z) { sketch_host_panels(cc, H, pc, om, ps, Y, Z); });
   });
@@ -1313,7 +1324,9 @@ lr_status lr_subspace_iter_host(lr_handle h, const lr_mat* A_host, int64_t panel
   return guarded(h, [&] {
     LR_REQUIRE(A_host && A_host->data, LR_ERR_INVALID_ARG, "A_host is NULL");
     LR_REQUIRE(A_host->dtype == LR_F32 && A_host->col_major == 0, LR_ERR_DTYPE, "A_host must be F32 row-major");
-    LR_REQUIRE(A_host->rows >= 1 && A_host->cols >= 1 && A_host->ld >= A_host->cols, LR_ERR_SHAPE, "bad A_host");
+    LR_REQUIRE(A_host->rows >= 1 && A_host->cols >= 1 &&
+                   (A_host->ld >= A_host->cols || (opts && opts->host_panels)),
+               LR_ERR_SHAPE, "bad A_host");
     LR_REQUIRE(panel_cols >= 1, LR_ERR_INVALID_ARG, "panel_cols must be positive");
     cudaPointerAttributes pa{};
     LR_CHECK_CUDA(cudaPointerGetAttributes(&pa, A_host->data));
@@ -1328,8 +1341,11 @@ lr_status lr_subspace_iter_host(lr_handle h, const lr_mat* A_host, int64_t panel
     Mat om = check_thin(Omega, a.n, ell, "Omega");
     Outs o = check_outs(a, k, U, S, V);
     Ctx c = make_ctx(h, opts, stream);
-    HostA H{static_cast<const float*>(A_host->data), a.m, a.n, A_host->ld};
-    const int64_t pc = std::min<int64_t>(panel_cols, a.n);
+    const bool panels = opts && opts->host_panels;
+    LR_REQUIRE(!panels || (panel_cols % 4 == 0 && A_host->ld == panel_cols), LR_ERR_SHAPE,
+               "panel layout: panel_cols must be a multiple of 4 and A_host->ld == panel_cols");
+    HostA H{static_cast<const float*>(A_host->data), a.m, a.n, A_host->ld, panels};
+    const int64_t pc = panels ? panel_cols : std::min<int64_t>(panel_cols, a.n);
     Viewer vw;
     vw.range = [&](Ctx& cc, const Mat& X, Mat Y) { host_views(cc, H, pc, &X, &Y, nullptr, nullptr); };
     vw.corange = [&](Ctx& cc, const Mat& W, Mat Z) { host_views(cc, H, pc, nullptr, nullptr, &W, &Z); };

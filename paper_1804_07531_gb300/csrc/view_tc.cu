@@ -540,8 +540,23 @@ __global__ void split_tf32_kernel(const float* __restrict__ src, int64_t lds, fl
 }
 
 // ------------------------------------------------------------------ host
+// Grid of a view launch.  Stream-K by default: min(SMs, iterations), each
+// CTA a contiguous range of (tile, k-block) iterations.  When the thin
+// operand is larger than L2 and there are fewer output tiles than SMs (the
+// co-range view of a tall panel), the CTAs that share a tile start at
+// different k-blocks under stream-K, so every CTA streams its own rows of the
+// operand from HBM (about one full read of it per tile).  There the grid is
+// tiles x floor(SMs / tiles) instead: each CTA takes one K slice of one tile,
+// the CTAs of a slice start at the same k-block and advance together, and
+// each block of operand rows is read from HBM once and from L2 by the others.
+inline int view_grid(int64_t iters_total, int tiles, int sms, double b_bytes) {
+  if (b_bytes > 48.0 * 1024 * 1024 && tiles > 0 && tiles < sms) return tiles * (sms / tiles);
+  return int(std::min<int64_t>(sms, iters_total));
+}
+
 template <int MODE, int NCOL>
-void launch_ncol(const CUtensorMap& ma, const CUtensorMap& mb, ViewParams p, int tiles, int sms, cudaStream_t s) {
+void launch_ncol(const CUtensorMap& ma, const CUtensorMap& mb, ViewParams p, int tiles, int sms, cudaStream_t s,
+                 double b_bytes = 0) {
   constexpr int NS = 2;
   constexpr int STAGES = (NCOL <= 128) ? 4 : 3;
   using C = Cfg<MODE, NS, NCOL, STAGES>;
@@ -554,7 +569,7 @@ void launch_ncol(const CUtensorMap& ma, const CUtensorMap& mb, ViewParams p, int
     attr_set[dev & 63] = true;
   }
   p.iters_total = int64_t(tiles) * p.kblocks;
-  int grid = int(std::min<int64_t>(sms, p.iters_total));
+  int grid = view_grid(p.iters_total, tiles, sms, b_bytes);
   if (grid <= 0) return;
   kern<<<grid, kThreads, C::kSmem, s>>>(ma, mb, p);
   LR_LAUNCH_CHECK();
@@ -598,11 +613,12 @@ void view_bf16(const ViewBf16Args& a, cudaStream_t s) {
     p.m_out = a.n;
     p.kblocks = ceil_div(a.rows, 64);
     const int tiles = ceil_div(a.n, 256);
+    const double bb = double(a.rows) * ncol * 2;  // the BF16 operand rows this launch reads
     switch (ncol) {
-      case 32: launch_ncol<1, 32>(ma, mb, p, tiles, sms, s); break;
-      case 64: launch_ncol<1, 64>(ma, mb, p, tiles, sms, s); break;
-      case 128: launch_ncol<1, 128>(ma, mb, p, tiles, sms, s); break;
-      default: launch_ncol<1, 256>(ma, mb, p, tiles, sms, s); break;
+      case 32: launch_ncol<1, 32>(ma, mb, p, tiles, sms, s, bb); break;
+      case 64: launch_ncol<1, 64>(ma, mb, p, tiles, sms, s, bb); break;
+      case 128: launch_ncol<1, 128>(ma, mb, p, tiles, sms, s, bb); break;
+      default: launch_ncol<1, 256>(ma, mb, p, tiles, sms, s, bb); break;
     }
   }
 }
@@ -611,7 +627,7 @@ void view_bf16(const ViewBf16Args& a, cudaStream_t s) {
 namespace {
 template <int MODE, int NCOL, bool SPLITB = false, bool OUT64 = false>
 void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMap& mbl, ViewParams p, int tiles,
-                 int sms, cudaStream_t s) {
+                 int sms, cudaStream_t s, double b_bytes = 0) {
   constexpr int STAGES = (NCOL <= 64) ? 4 : (NCOL <= 128) ? 3 : 2;
   using C = CfgT<MODE, NCOL, STAGES>;
   auto kern = view_tf32x3_kernel<MODE, NCOL, STAGES, SPLITB, OUT64>;
@@ -623,7 +639,7 @@ void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMa
     attr_set[dev & 63] = true;
   }
   p.iters_total = int64_t(tiles) * p.kblocks;
-  const int grid = int(std::min<int64_t>(sms, p.iters_total));
+  const int grid = view_grid(p.iters_total, tiles, sms, b_bytes);
   if (grid <= 0) return;
   kern<<<grid, kThreadsT, C::kSmem, s>>>(ma, mbh, mbl, p);
   LR_LAUNCH_CHECK();
@@ -694,11 +710,12 @@ void view_tf32x3(const ViewTf32Args& a, cudaStream_t s) {
     p.m_out = a.n;
     p.kblocks = ceil_div(a.rows, 32);
     const int tiles = ceil_div(a.n, 128);
+    const double bb = double(a.rows) * ncol * 8;  // the TF32 hi + lo operand rows this launch reads
     switch (ncol) {
-      case 32: launch_tf32<1, 32>(ma, mh, ml, p, tiles, sms, s); break;
-      case 64: launch_tf32<1, 64>(ma, mh, ml, p, tiles, sms, s); break;
-      case 128: launch_tf32<1, 128>(ma, mh, ml, p, tiles, sms, s); break;
-      default: launch_tf32<1, 256>(ma, mh, ml, p, tiles, sms, s); break;
+      case 32: launch_tf32<1, 32>(ma, mh, ml, p, tiles, sms, s, bb); break;
+      case 64: launch_tf32<1, 64>(ma, mh, ml, p, tiles, sms, s, bb); break;
+      case 128: launch_tf32<1, 128>(ma, mh, ml, p, tiles, sms, s, bb); break;
+      default: launch_tf32<1, 256>(ma, mh, ml, p, tiles, sms, s, bb); break;
     }
   }
 }

@@ -384,3 +384,32 @@ def test_block_krylov_from_host_buffers_matches_device_run(c1, dtype):
         a64 = a32.astype(np.float64)
         uo, so, vo = Al.block_krylov(a64, om.astype(np.float64), k, v)
         print(check_tsvd(a64, u, s, vv, uo, so, vo))
+
+
+@pytest.mark.parametrize("algo", ["single_pass", "subspace"])
+def test_host_stream_panel_layout_matches_row_major(algo):
+    """A stored as contiguous column panels (opts.host_panels; ragged last
+    panel) gives the same factorisation as the row-major host layout."""
+    m, n, k, p, pc = 4096, 3000, 20, 10, 1024
+    a64 = S.usv(m, n, S.sigma_config("inv", n), 95, 96) + 1e-5 * S.gaussian(m, n, seed=97)
+    a32 = a64.astype(np.float32)
+    npan = (n + pc - 1) // pc
+    panels = np.zeros((npan, m, pc), dtype=np.float32)
+    for i in range(npan):
+        w = min(pc, n - i * pc)
+        panels[i, :, :w] = a32[:, i * pc:i * pc + w]
+    ah = torch.tensor(a32).pin_memory()
+    ap = torch.tensor(panels).pin_memory()
+    om = torch.tensor(S.gaussian(n, k + p, seed=98).astype(np.float32))
+    if algo == "single_pass":
+        ps = torch.tensor(S.gaussian(m, 2 * (k + p), seed=99).astype(np.float32))
+        u1, s1, v1 = api().single_pass_host(ah, k, om, ps, panel_cols=pc)
+        u2, s2, v2 = api().single_pass_host(ap, k, om, ps, n=n)
+    else:
+        u1, s1, v1 = api().subspace_iter_host(ah, k, p, 3, om, panel_cols=pc)
+        u2, s2, v2 = api().subspace_iter_host(ap, k, p, 3, om, n=n)
+    assert_status_ok()
+    assert np.abs(f64(s1) - f64(s2)).max() / f64(s1)[0] < 1e-6
+    a = a32.astype(np.float64)
+    assert abs(Al.frob_error(a, f64(u1), f64(s1), f64(v1)) - Al.frob_error(a, f64(u2), f64(s2), f64(v2))) \
+        < 1e-6 * Al.frob_error(a, f64(u1), f64(s1), f64(v1))
