@@ -108,40 +108,43 @@ inline bool tma_ok(const void* p, int64_t ld) {
   return (reinterpret_cast<uintptr_t>(p) & 15) == 0 && ld % 4 == 0;
 }
 
-// C (M x N) = alpha op(A) op(B) + beta C.  Tall products with a short inner
-// dimension -- the applications Q = Y R^{-1} and Y_b -= Q_prev C of the thin
-// QR and the lifts U = Q W -- run on the tensor cores as a co-range view of
-// A^T (A^T row-major = A col-major; the small B split into TF32 hi/lo with
-// alpha folded in); the rest on the SIMT kernel.
+// C (M x N) = alpha op(A) op(B) + beta C.  Tall products -- the applications
+// Q = Y R^{-1} and Y_b -= Q_prev C of the thin QR, the lifts U = Q W -- run
+// on the tensor cores as a co-range view of A^T (A^T row-major = A
+// col-major; op(B) split into TF32 hi/lo with alpha folded in), in groups of
+// at most 256 columns of C; the rest on the SIMT kernel.
 void gemm(Ctx& c, int64_t M, int64_t N, int64_t K, bool ta, const float* A, int64_t lda, bool tb, const float* B,
           int64_t ldb, float* C, int64_t ldc, float alpha = 1.f, float beta = 0.f, const int* run_if = nullptr) {
-  const bool tc = !ta && !tb && M >= 2048 && K >= 1 && K <= 256 && N <= 256 && (beta == 0.f || beta == 1.f) &&
-                  tma_ok(A, lda);
+  // (N > 1024 would mean over four launches that each re-read A and cover
+  // few output tiles: the SIMT kernel's single launch serves that shape)
+  const bool tc = !ta && M >= 2048 && K >= 1 && N <= 1024 && (beta == 0.f || beta == 1.f) && tma_ok(A, lda);
   if (tc) {
     ArenaScope sc(c.ar);
     const int64_t ldw = round4(K);
     float* wh = c.ar.take<float>(size_t(ldw) * N);
     float* wl = c.ar.take<float>(size_t(ldw) * N);
     if (c.measure) return;
-    split_tf32(B, ldb, wh, wl, ldw, K, N, c.s, alpha);
+    split_tf32(B, ldb, wh, wl, ldw, K, N, c.s, alpha, tb);  // op(B), K x N
     if (beta == 0.f) zero_f32(C, M, N, ldc, c.s, run_if);  // a skipped product leaves C as it was
-    ViewTf32Args a;
-    a.device = c.h->device;
-    a.mode = 1;
-    a.A = A;
-    a.lda = lda;
-    a.row0 = 0;
-    a.rows = K;
-    a.n = M;
-    a.Bhi = wh;
-    a.Blo = wl;
-    a.ldb = ldw;
-    a.ell = int(N);
-    a.out = C;
-    a.ldo = ldc;
-    a.status = c.status;
-    a.run_if = run_if;
-    view_tf32x3(a, c.s);
+    for (int64_t g0 = 0; g0 < N; g0 += 256) {
+      ViewTf32Args a;
+      a.device = c.h->device;
+      a.mode = 1;
+      a.A = A;
+      a.lda = lda;
+      a.row0 = 0;
+      a.rows = K;
+      a.n = M;
+      a.Bhi = wh + g0 * ldw;
+      a.Blo = wl + g0 * ldw;
+      a.ldb = ldw;
+      a.ell = int(std::min<int64_t>(256, N - g0));
+      a.out = C + g0 * ldc;
+      a.ldo = ldc;
+      a.status = c.status;
+      a.run_if = run_if;
+      view_tf32x3(a, c.s);
+    }
     return;
   }
   if (c.measure) return;
@@ -159,22 +162,25 @@ void gram64(Ctx& c, int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
             double* C64, int64_t ldc, const int* run_if = nullptr) {
   if (c.measure) return;
   LR_CHECK_CUDA(cudaMemsetAsync(C64, 0, size_t(ldc) * N * sizeof(double), c.s));
-  if (K >= 1024 && N <= 256 && tma_ok(A, lda) && tma_ok(B, ldb)) {
-    // tall panels: tensor cores, FP32 products per CTA, FP64 across CTAs
-    GramTf32Args a;
-    a.device = c.h->device;
-    a.P = A;
-    a.lda = lda;
-    a.a = int(M);
-    a.Q = B;
-    a.ldb = ldb;
-    a.b = int(N);
-    a.m = K;
-    a.C64 = C64;
-    a.ldc = ldc;
-    a.status = c.status;
-    a.run_if = run_if;
-    gram_tf32x3(a, c.s);
+  if (K >= 1024 && tma_ok(A, lda) && tma_ok(B, ldb)) {
+    // tall panels: tensor cores, FP32 products per CTA, FP64 across CTAs, in
+    // groups of at most 256 columns of the result
+    for (int64_t g0 = 0; g0 < N; g0 += 256) {
+      GramTf32Args a;
+      a.device = c.h->device;
+      a.P = A;
+      a.lda = lda;
+      a.a = int(M);
+      a.Q = B + g0 * ldb;
+      a.ldb = ldb;
+      a.b = int(std::min<int64_t>(256, N - g0));
+      a.m = K;
+      a.C64 = C64 + g0 * ldc;
+      a.ldc = ldc;
+      a.status = c.status;
+      a.run_if = run_if;
+      gram_tf32x3(a, c.s);
+    }
     return;
   }
   GemmArgs g;

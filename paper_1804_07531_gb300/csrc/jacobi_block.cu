@@ -45,8 +45,8 @@
 // exchange and pass the same barriers afterwards.
 //
 // Rotation: zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| +
-// sqrt(1 + zeta^2)) (computed without forming zeta, see angle()),
-// c = 1 / sqrt(1 + t^2), s = c t, applied when gamma^2 > tol^2 alpha beta
+// sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2), s = c t (formed through cos 2theta
+// without a division, see angle()), applied when gamma^2 > tol^2 alpha beta
 // (tol = eps sqrt(n)).  t only has to be close (an
 // inexact angle is still a rotation); c is the refined reciprocal square
 // root, so c^2 + s^2 = 1 to about an ulp.  Outputs: sigma_i = |w_i| / |v_i|,
@@ -137,21 +137,30 @@ __device__ __forceinline__ float rsqrt_nr(float d) {
 }
 
 // The rotation of a pair with |x|^2 = al, |y|^2 = be, x . y = ga (the same
-// values in the group's lanes, so the same decision).  With d = be - al,
-// t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = d / (2 ga), is the
-// same number as sign(d) 2 ga / (|d| + sqrt(d^2 + 4 ga^2)), which needs one
-// square root and one reciprocal and no division first.
+// values in the group's lanes, so the same decision).  With d = be - al and
+// r = 1 / sqrt(d^2 + 4 ga^2): cos 2theta = q = |d| r, and with
+// u = 1 / sqrt((1 + q) / 2) = 1 / cos theta,
+//   c = ((1 + q) / 2) u,   s = sign(d) ga r u,
+// which is the angle of t = sign(d) 2 ga / (|d| + sqrt(d^2 + 4 ga^2)).  The
+// dependency chain holds two reciprocal square roots and no division; s
+// comes from ga directly, so small angles lose no relative accuracy, and
+// c^2 + s^2 = u^2 (1 + q) / 2 = 1 up to the (Newton-refined) u.  Where
+// d^2 + 4 ga^2 leaves the normal range the same t is formed through zeta.
 __device__ __forceinline__ bool angle(float al, float be, float ga, float tol2, float& c, float& s) {
   if (!(al > 0.f && be > 0.f && ga * ga > tol2 * al * be)) return false;
   const float d = be - al, g2 = ga + ga;
   const float h = fmaf(d, d, g2 * g2);
-  float t;
-  if (h < 3.0e38f) {
-    t = copysignf(1.f, d) * __fdividef(g2, fabsf(d) + h * rsqrtf(h));
-  } else {  // d^2 + 4 ga^2 overflows: the same t through zeta
-    const float zeta = __fdividef(d, g2), az = fabsf(zeta);
-    t = az < 1e18f ? copysignf(__fdividef(1.f, az + sqrtf(fmaf(zeta, zeta, 1.f))), zeta) : __fdividef(0.5f, zeta);
+  if (h > 1.0e-30f && h < 3.0e38f) {
+    const float r = rsqrtf(h);
+    const float hq = fmaf(0.5f, fabsf(d) * r, 0.5f);
+    const float u = rsqrt_nr(hq);
+    c = hq * u;
+    s = copysignf(1.f, d) * (ga * r) * u;
+    return true;
   }
+  const float zeta = __fdividef(d, g2), az = fabsf(zeta);
+  const float t = az < 1e18f ? copysignf(__fdividef(1.f, az + sqrtf(fmaf(zeta, zeta, 1.f))), zeta)
+                             : __fdividef(0.5f, zeta);
   c = rsqrt_nr(fmaf(t, t, 1.f));
   s = c * t;
   return true;

@@ -102,8 +102,10 @@ struct GramTf32Args {
   const int* run_if = nullptr;
 };
 void gram_tf32x3(const GramTf32Args& a, cudaStream_t s);
+// hi + lo = scale * src (rows x cols, column-major), or scale * src^T when
+// trans (src then cols x rows, column-major).
 void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd, int64_t rows, int64_t cols,
-                cudaStream_t s, float scale = 1.f);
+                cudaStream_t s, float scale = 1.f, bool trans = false);
 
 // ---------------------------------------------------------- elementwise
 // run_if (device int, optional): zero only when *run_if != 0.

@@ -529,10 +529,11 @@ __global__ void __launch_bounds__(kThreadsT, 1)
 }
 
 __global__ void split_tf32_kernel(const float* __restrict__ src, int64_t lds, float* __restrict__ hi,
-                                  float* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols, float scale) {
+                                  float* __restrict__ lo, int64_t ldd, int64_t rows, int64_t cols, float scale,
+                                  int trans) {
   for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
     for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
-      const float x = scale * src[r + c * lds];
+      const float x = scale * (trans ? src[c + r * lds] : src[r + c * lds]);
       const float h = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
       hi[r + c * ldd] = h;
       lo[r + c * ldd] = x - h;
@@ -647,9 +648,9 @@ void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMa
 }  // namespace
 
 void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd, int64_t rows, int64_t cols,
-                cudaStream_t s, float scale) {
+                cudaStream_t s, float scale, bool trans) {
   if (rows <= 0 || cols <= 0) return;
-  split_tf32_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, scale);
+  split_tf32_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(src, lds, hi, lo, ldd, rows, cols, scale, trans ? 1 : 0);
   LR_LAUNCH_CHECK();
 }
 
