@@ -219,6 +219,52 @@ lr_status lr_block_krylov_host(lr_handle handle, const lr_mat* A_host, int k, in
                                const lr_mat* Omega_host, lr_mat* U_host, lr_mat* S_host, lr_mat* V_host,
                                const lr_opts* opts, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Matrix-free operators (Section 4.2.3; the paper's J applied by direct and
+ * adjoint methods).
+ * ------------------------------------------------------------------- */
+
+/* J (rows x cols) as a callback: apply(ctx, 0, X, ldx, ncols, Y, ldy, stream)
+ * writes Y = J X (X: cols x ncols, Y: rows x ncols); apply(ctx, 1, ...)
+ * writes Y = J^T X (X: rows x ncols, Y: cols x ncols).  X and Y are F32
+ * column-major device arrays owned by the library (X must not be written),
+ * and the work is enqueued on `stream` (the stream of the calling entry
+ * point); the callback returns 0 on success, anything else aborts the call
+ * with LR_ERR_INVALID_ARG.  The callback must not use the same lr_handle. */
+typedef int (*lr_apply_fn)(void* ctx, int transpose, const float* X, int64_t ldx, int64_t ncols, float* Y,
+                           int64_t ldy, void* stream);
+typedef struct {
+  int64_t rows, cols;
+  lr_apply_fn apply;
+  void* ctx;
+} lr_operator;
+
+/* Alg. 2 with J given as an operator (every view one callback).  Arguments
+ * and outputs as lr_subspace_iter with A replaced by J. */
+lr_status lr_subspace_iter_op(lr_handle handle, const lr_operator* J, int k, int p, int v, const lr_mat* Omega,
+                              lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts, void* stream);
+
+/* Alg. 4 (Nystrom / prolonged sketch): approximate rank-k EVD V diag(Lambda2)
+ * V^T of J^T J from v >= 2 views of J.  Omega (F32 column-major) is
+ * cols x (k+p) for even v (the start of Alg. 3 on J; orthonormalised for
+ * v = 2) and rows x (k+p) for odd v (Alg. 3 on J^T).  The shift is
+ * nu = 2^-23 ||Y_r||_F (the paper's 2.2e-16 ||Y_r|| scaled to FP32; subtracted
+ * again, eigenvalues below it clipped to 0).  k + p <= 128 (the Cholesky of
+ * the (k+p) x (k+p) core runs in one CTA).  Outputs: V (cols x k, F32
+ * column-major, orthonormal, each column's largest entry positive),
+ * Lambda2 (k F32, descending).  Errors as lr_subspace_iter; a Cholesky
+ * breakdown sets LR_ERR_BREAKDOWN in the status word. */
+lr_status lr_nystrom_tevd(lr_handle handle, const lr_operator* J, int k, int p, int v, const lr_mat* Omega,
+                          lr_mat* V, lr_mat* Lambda2, const lr_opts* opts, void* stream);
+
+/* Alg. 5 (pinched sketch): rank-k EVD of J^T J from v >= 2 views of J:
+ * Q_r from v - 1 views (Alg. 3 on J^T from an Omega of rows x (k+p) for
+ * even v, on J from cols x (k+p) for odd v), B_c = J Q_r, and the EVD of
+ * B_c^T B_c through the SVD of B_c's triangular factor.  Outputs as
+ * lr_nystrom_tevd. */
+lr_status lr_pinched_tevd(lr_handle handle, const lr_operator* J, int k, int p, int v, const lr_mat* Omega,
+                          lr_mat* V, lr_mat* Lambda2, const lr_opts* opts, void* stream);
+
 /* Reverse pass of lr_subspace_iter for the loss L = sum_i dS_i sigma_i
  * (dS: k weights, F32): writes dA = dL/dA (m x n, F32 row-major, same shape
  * as A, overwritten).  The forward views are recomputed, not stored.  A must

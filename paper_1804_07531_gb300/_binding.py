@@ -30,7 +30,8 @@ EXPORTS = [
     "lr_create", "lr_destroy", "lr_status_string", "lr_last_error", "lr_workspace_size",
     "lr_set_workspace", "lr_get_status", "lr_sketch", "lr_sketch_chained", "lr_orth",
     "lr_subspace_iter", "lr_single_pass", "lr_block_krylov", "lr_rowwise_single_pass",
-    "lr_single_pass_host", "lr_subspace_iter_host", "lr_block_krylov_host", "lr_subspace_iter_backward", "lr_set_trace", "lr_trace_read",
+    "lr_single_pass_host", "lr_subspace_iter_host", "lr_block_krylov_host", "lr_subspace_iter_op",
+    "lr_nystrom_tevd", "lr_pinched_tevd", "lr_subspace_iter_backward", "lr_set_trace", "lr_trace_read",
     "lr_kernel_launches", "lr_sketch_range_static", "lr_sketch_range_static_status", "lr_selftest_bounded_wait",
 ]
 TRACE_KINDS = {"view_range": 0, "view_corange": 1, "orth": 2, "core_svd": 3, "view_dual": 4}
@@ -45,6 +46,16 @@ class LrOpts(ctypes.Structure):
     _fields_ = [("l_c", ctypes.c_int32), ("enhanced", ctypes.c_int32), ("split_last", ctypes.c_int32),
                 ("shifted_fallback", ctypes.c_int32), ("band_mb", ctypes.c_int32),
                 ("host_panels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
+# int apply(void* ctx, int transpose, const float* X, int64_t ldx, int64_t ncols, float* Y, int64_t ldy,
+#           void* stream)
+APPLY_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64,
+                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
+
+
+class LrOperator(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("apply", APPLY_FN), ("ctx", ctypes.c_void_p)]
 
 
 class LowrankError(RuntimeError):
@@ -89,6 +100,10 @@ def lib():
             L.lr_single_pass_host.argtypes = [P, M, I64, I, M, M, M, M, M, O, P]
             L.lr_subspace_iter_host.argtypes = [P, M, I64, I, I, I, M, M, M, M, O, P]
             L.lr_block_krylov_host.argtypes = [P, M, I, I, I, M, M, M, M, O, P]
+            OP = ctypes.POINTER(LrOperator)
+            L.lr_subspace_iter_op.argtypes = [P, OP, I, I, I, M, M, M, M, O, P]
+            L.lr_nystrom_tevd.argtypes = [P, OP, I, I, I, M, M, M, O, P]
+            L.lr_pinched_tevd.argtypes = [P, OP, I, I, I, M, M, M, O, P]
             L.lr_subspace_iter_backward.argtypes = [P, M, I, I, I, M, M, M, O, P]
             L.lr_set_trace.argtypes = [P, I]
             L.lr_trace_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I]

@@ -12,13 +12,13 @@ import ctypes
 
 import torch
 
-from ._binding import (Handle, LowrankError, LrMat, _opts, _stream, col_major, empty_cm, lib, mat_a,
-                       mat_thin)
+from ._binding import (APPLY_FN, Handle, LowrankError, LrMat, LrOperator, _opts, _stream, col_major, empty_cm, lib,
+                       mat_a, mat_thin)
 
 __all__ = [
     "sketch", "sketch_chained", "orth", "subspace_iter", "single_pass", "block_krylov",
     "rowwise_single_pass", "subspace_iter_backward", "single_pass_host", "subspace_iter_host", "block_krylov_host",
-    "device_status",
+    "Operator", "MatrixOperator", "subspace_iter_op", "nystrom_tevd", "pinched_tevd", "device_status",
     "LowrankError",
 ]
 
@@ -291,3 +291,112 @@ def block_krylov_host(a_host, k, p, v, omega_host, out=None, enhanced=False, spl
         _call(h, lib().lr_block_krylov_host, _p(mh), k, p, v, _p(mats[0]), _p(mats[1]), _p(mats[2]), _p(mats[3]),
               ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return u, s, vv
+
+
+# ------------------------------------------------------- operators
+class _DeviceArray:
+    """A column-major float32 device array described by __cuda_array_interface__
+    (wrapped by torch.as_tensor without a copy)."""
+
+    def __init__(self, ptr, rows, cols, ld):
+        self.__cuda_array_interface__ = {"shape": (int(rows), int(cols)), "typestr": "<f4",
+                                         "data": (int(ptr), False), "strides": (4, 4 * int(ld)), "version": 2}
+
+
+class Operator:
+    """A matrix-free J (rows x cols) for the operator entry points (Section
+    4.2.3: J applied by direct and adjoint methods).  apply(transpose, X, Y)
+    must write Y = J X (transpose = 0; X cols x ncols, Y rows x ncols) or
+    Y = J^T X (transpose = 1) into the given column-major float32 CUDA
+    tensors, on the current stream."""
+
+    def __init__(self, rows, cols, apply, device=None):
+        self.rows, self.cols = int(rows), int(cols)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self._apply = apply
+        self.error = None
+
+        def cb(ctx, transpose, xp, ldx, ncols, yp, ldy, stream):
+            try:
+                rx, ry = (self.cols, self.rows) if transpose == 0 else (self.rows, self.cols)
+                x = torch.as_tensor(_DeviceArray(xp, rx, ncols, ldx), device=self.device)
+                y = torch.as_tensor(_DeviceArray(yp, ry, ncols, ldy), device=self.device)
+                self._apply(int(transpose), x, y)
+                return 0
+            except Exception as e:  # reported to the caller by the entry point's status
+                self.error = e
+                return 1
+
+        self._cb = APPLY_FN(cb)
+        self.c = LrOperator(self.rows, self.cols, self._cb, None)
+
+
+class MatrixOperator(Operator):
+    """J as a device matrix (float32 or bfloat16, row-major), applied by this
+    library's own views on a handle of its own."""
+
+    def __init__(self, j):
+        if not j.is_cuda or j.stride(1) != 1:
+            raise ValueError("J must be a row-major CUDA matrix")
+        self.j = j
+        self.h = Handle(j.device.index)
+
+        def apply(transpose, x, y):
+            m, n = self.j.shape
+            self.h.reserve(m, n, max(1, x.shape[1]))
+            mA, mx, my = mat_a(self.j), mat_thin(x), mat_thin(y)
+            o = _opts()
+            if transpose == 0:
+                st = lib().lr_sketch(self.h.h, _p(mA), _p(mx), None, _p(my), None, ctypes.byref(o),
+                                     ctypes.c_void_p(_stream()))
+            else:
+                st = lib().lr_sketch(self.h.h, _p(mA), None, _p(mx), None, _p(my), ctypes.byref(o),
+                                     ctypes.c_void_p(_stream()))
+            self.h.check(st)
+
+        super().__init__(j.shape[0], j.shape[1], apply, device=j.device.index)
+
+
+def subspace_iter_op(op, k, p, v, omega, stream=None):
+    """Alg. 2 with J given as an Operator: (U, S, V)."""
+    dev = op.device
+    h = Handle.get(dev)
+    h.reserve(op.rows, op.cols, k + p, 0, v)
+    omega = col_major(omega.to(device=dev, dtype=torch.float32))
+    u = empty_cm(op.rows, k, dev)
+    s = torch.empty(k, dtype=torch.float32, device=dev)
+    vv = empty_cm(op.cols, k, dev)
+    mats = [mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts()
+    _call(h, lib().lr_subspace_iter_op, ctypes.byref(op.c), k, p, v, _p(mats[0]), _p(mats[1]), _p(mats[2]),
+          _p(mats[3]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+def _tevd(fn, op, k, p, v, omega, stream):
+    dev = op.device
+    h = Handle.get(dev)
+    h.reserve(op.rows, op.cols, k + p, 0, v)
+    omega = col_major(omega.to(device=dev, dtype=torch.float32))
+    vv = empty_cm(op.cols, k, dev)
+    lam2 = torch.empty(k, dtype=torch.float32, device=dev)
+    mats = [mat_thin(omega), mat_thin(vv), mat_thin(lam2)]
+    o = _opts()
+    st = fn(h.h, ctypes.byref(op.c), k, p, v, _p(mats[0]), _p(mats[1]), _p(mats[2]), ctypes.byref(o),
+            ctypes.c_void_p(_stream(stream)))
+    if st != 0 and op.error is not None:
+        raise op.error
+    h.check(st)
+    return vv, lam2
+
+
+def nystrom_tevd(op, k, p, v, omega, stream=None):
+    """Alg. 4: (V, Lambda2), the Nystrom rank-k EVD of J^T J from v >= 2 views
+    of J.  omega: cols x (k+p) for even v, rows x (k+p) for odd v."""
+    return _tevd(lib().lr_nystrom_tevd, op, k, p, v, omega, stream)
+
+
+def pinched_tevd(op, k, p, v, omega, stream=None):
+    """Alg. 5: (V, Lambda2), the pinched rank-k EVD of J^T J from v >= 2 views
+    of J.  omega: rows x (k+p) for even v, cols x (k+p) for odd v."""
+    return _tevd(lib().lr_pinched_tevd, op, k, p, v, omega, stream)

@@ -589,6 +589,138 @@ void run_subspace(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, O
   }
 }
 
+// ---------------------------------------------------- Algs. 3, 4, 5
+// An operator J (rows x cols) given by the caller's callback, as the views
+// of the schedules see it; transposed when `t` (the views of J^T).
+Viewer op_viewer(const lr_operator* J, bool t) {
+  auto call = [J](Ctx& c, int transpose, const Mat& X, Mat Y) {
+    if (c.measure) return;
+    const int rc = J->apply(J->ctx, transpose, X.p, X.ld, X.cols, Y.p, Y.ld, c.s);
+    LR_REQUIRE(rc == 0, LR_ERR_INVALID_ARG, "the operator's callback failed (returned " + std::to_string(rc) + ")");
+    LR_CHECK_CUDA(cudaGetLastError());
+  };
+  Viewer vw;
+  vw.range = [call, t](Ctx& c, const Mat& X, Mat Y) { call(c, t ? 1 : 0, X, Y); };
+  vw.corange = [call, t](Ctx& c, const Mat& W, Mat Z) { call(c, t ? 0 : 1, W, Z); };
+  return vw;
+}
+
+// Alg. 3 on an operator B (rows_b x cols_b, views vw), v >= 1 views from
+// Q_r = Omega (cols_b x ell): odd j Q_c = qr(B Q_r) into Qc (rows_b x ell),
+// even j Q_r = qr(B^T Q_c) into Qr (cols_b x ell); returns the last one.
+Mat run_qrqc(Ctx& c, const Viewer& vw, const Mat& Om, int v, Mat Qc, Mat Qr) {
+  Mat cur = Om;
+  for (int j = 1; j <= v; ++j) {
+    if (j % 2 == 1) {
+      vw.range(c, cur, Qc);
+      orth(c, Qc, nullptr);
+    } else {
+      vw.corange(c, Qc, Qr);
+      orth(c, Qr, nullptr);
+      cur = Qr;
+    }
+  }
+  return v % 2 == 0 ? Qr : Qc;
+}
+
+// The columns of V (n x k) with the sign that makes each one's largest entry positive.
+void sign_columns(Ctx& c, Mat V, int k) {
+  if (!c.measure) fix_signs(V.p, V.ld, V.rows, V.p, 0, 0, k, c.s);
+}
+
+// Alg. 4: J (m x n) by callback; Omega n x ell (v even) or m x ell (v odd).
+void run_nystrom(Ctx& c, const lr_operator* J, int k, int ell, int v, const Mat& Om, Mat Vout, float* lam2) {
+  ArenaScope sc(c.ar);
+  const int64_t m = J->rows, n = J->cols;
+  const int64_t mx = std::max(m, n);
+  Mat Qa{c.ar.take<float>(size_t(mx) * ell), 0, ell, mx};  // Q_c of the start operator
+  Mat Qr{c.ar.take<float>(size_t(n) * ell), n, ell, n};
+  Mat Y{c.ar.take<float>(size_t(m) * ell), m, ell, m};
+  Mat Yr{c.ar.take<float>(size_t(n) * ell), n, ell, n};
+  Mat Ft{c.ar.take<float>(size_t(n) * ell), n, ell, n};
+  double* B = c.ar.take<double>(size_t(ell) * ell);
+  double* Rf = c.ar.take<double>(size_t(ell) * ell);
+  double* ssq = c.ar.take<double>(1);
+  float* Rinv = c.ar.take<float>(size_t(ell) * ell);
+  float* L = c.ar.take<float>(size_t(ell) * ell);
+  float* Rt = c.ar.take<float>(size_t(ell) * ell);
+  float* Sv = c.ar.take<float>(size_t(ell));
+  const Viewer vj = op_viewer(J, false), vt = op_viewer(J, true);
+  if (c.measure) {
+    orth(c, Mat{nullptr, mx, ell, mx}, nullptr);
+    core_svd(c, nullptr, ell, nullptr, nullptr, nullptr);
+    gemm(c, n, ell, ell, false, nullptr, n, false, nullptr, ell, nullptr, n);
+    return;
+  }
+  // Q_r: orth(Omega) (v = 2), Alg. 3 on J (v even) or on J^T (v odd), v - 2 views
+  Mat q;
+  if (v == 2) {
+    copy_f32(Om.p, Om.ld, Qr.p, Qr.ld, n, ell, c.s);
+    orth(c, Qr, nullptr);
+    q = Qr;
+  } else if (v % 2 == 0) {
+    Qa.rows = m;
+    Qa.ld = m;
+    q = run_qrqc(c, vj, Om, v - 2, Qa, Qr);
+  } else {  // J^T: its Q_c lives in the n-dimensional space
+    Mat qc{Qr.p, n, ell, n};
+    Mat qr2{Qa.p, m, ell, m};
+    q = run_qrqc(c, vt, Om, v - 2, qc, qr2);
+  }
+  vj.range(c, q, Y);                                   // J Q_r
+  vj.corange(c, Y, Yr);                                // Y_r = J^T (J Q_r)
+  constexpr float kEps32 = 1.0f / 8388608.0f;          // 2^-23
+  sumsq_f32(Yr.p, Yr.ld, n, ell, ssq, c.s);
+  shift_add_f32(Yr.p, Yr.ld, q.p, q.ld, n, ell, ssq, kEps32, c.s);    // Y_r += nu Q_r
+  gram64(c, ell, ell, n, q.p, q.ld, Yr.p, Yr.ld, B, ell);            // B = Q_r^T Y_r
+  symmetrize_f64(B, ell, c.s);                                         // (B + B^T) / 2
+  chol_inv(B, ell, Rinv, ell, nullptr, 0, true, CHOL_PLAIN, nullptr, c.status, c.s);  // C_L = R^T
+  gemm(c, n, ell, ell, false, Yr.p, Yr.ld, false, Rinv, ell, Ft.p, Ft.ld);          // F^T = Y_r R^{-1}
+  orth(c, Ft, Rf);                                     // F^T = Q_f R_f
+  core_svd(c, Rf, ell, L, Rt, Sv);                     // R_f = L diag(S) Rt^T
+  gemm(c, n, k, ell, false, Ft.p, Ft.ld, false, L, ell, Vout.p, Vout.ld);  // V = Q_f L_k
+  sign_columns(c, Vout, k);
+  sq_shift(Sv, k, ssq, kEps32, lam2, c.s);             // max(S^2 - nu, 0)
+}
+
+// Alg. 5: Q_r from v - 1 views (Alg. 3 on J^T from an m x ell Omega for
+// even v, on J from an n x ell Omega for odd v), B_c = J Q_r, EVD of
+// B_c^T B_c through B_c = Q R, R = L diag(S) Rt^T: eigenvectors Q_r Rt.
+void run_pinched(Ctx& c, const lr_operator* J, int k, int ell, int v, const Mat& Om, Mat Vout, float* lam2) {
+  ArenaScope sc(c.ar);
+  const int64_t m = J->rows, n = J->cols;
+  const int64_t mx = std::max(m, n);
+  Mat Qa{c.ar.take<float>(size_t(mx) * ell), 0, ell, mx};
+  Mat Qr{c.ar.take<float>(size_t(n) * ell), n, ell, n};
+  Mat Bc{c.ar.take<float>(size_t(m) * ell), m, ell, m};
+  double* Rb = c.ar.take<double>(size_t(ell) * ell);
+  float* L = c.ar.take<float>(size_t(ell) * ell);
+  float* Rt = c.ar.take<float>(size_t(ell) * ell);
+  float* Sv = c.ar.take<float>(size_t(ell));
+  const Viewer vj = op_viewer(J, false), vt = op_viewer(J, true);
+  if (c.measure) {
+    orth(c, Mat{nullptr, mx, ell, mx}, nullptr);
+    core_svd(c, nullptr, ell, nullptr, nullptr, nullptr);
+    return;
+  }
+  Mat q;
+  if (v % 2 == 0) {  // Alg. 3 on J^T, v - 1 (odd) views: its Q_c, n-dimensional
+    Mat qc{Qr.p, n, ell, n};
+    Mat qr2{Qa.p, m, ell, m};
+    q = run_qrqc(c, vt, Om, v - 1, qc, qr2);
+  } else {
+    Qa.rows = m;
+    Qa.ld = m;
+    q = run_qrqc(c, vj, Om, v - 1, Qa, Qr);
+  }
+  vj.range(c, q, Bc);                                  // B_c = J Q_r
+  orth(c, Bc, Rb);                                     // B_c = Q R
+  core_svd(c, Rb, ell, L, Rt, Sv);                     // R = L diag(S) Rt^T
+  gemm(c, n, k, ell, false, q.p, q.ld, false, Rt, ell, Vout.p, Vout.ld);  // V = Q_r Rt_k
+  sign_columns(c, Vout, k);
+  sq_shift(Sv, k, nullptr, 0.f, lam2, c.s);            // S^2
+}
+
 // ------------------------------------------------------------ Alg. 9
 void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o) {
   ArenaScope sc(c.ar);
@@ -1055,6 +1187,15 @@ void check_kpv(const AMat& A, int k, int p, int v, int vmin) {
 
 using namespace lr;
 
+namespace lr {
+namespace {
+void check_op(const lr_operator* J) {
+  LR_REQUIRE(J && J->apply, LR_ERR_INVALID_ARG, "operator (or its callback) is NULL");
+  LR_REQUIRE(J->rows >= 1 && J->cols >= 1, LR_ERR_SHAPE, "bad operator shape");
+}
+}  // namespace
+}  // namespace lr
+
 extern "C" {
 
 lr_status lr_create(lr_handle* handle, int device) {
@@ -1160,6 +1301,11 @@ lr_status lr_workspace_size(lr_handle h, int64_t m, int64_t n, int ell1, int ell
       measure([&](Ctx& c) { run_krylov(c, A, k, ell1, vv, Om, o); });
       measure([&](Ctx& c) { run_krylov_rowwise(c, A, k, ell1, vv, Om, o); });
       measure([&](Ctx& c) { run_rowwise_qb(c, A, k, ell1, Om, o); });
+      if (!A.bf16 && ell1 <= 128) {  // the operator forms (shapes only: no callback in measuring mode)
+        lr_operator op{m, n, nullptr, nullptr};
+        measure([&](Ctx& c) { run_nystrom(c, &op, k, ell1, vv, Om, Mat{nullptr, n, k, n}, nullptr); });
+        measure([&](Ctx& c) { run_pinched(c, &op, k, ell1, vv, Om, Mat{nullptr, n, k, n}, nullptr); });
+      }
       if (!A.bf16) measure([&](Ctx& c) { run_subspace_backward(c, A, 1, ell1, vv, Om, nullptr, nullptr, 0); });
       if (ell2 >= ell1) {
         Mat Ps{nullptr, m, ell2, m};
@@ -1403,6 +1549,58 @@ lr_status lr_block_krylov_host(lr_handle h, const lr_mat* A_host, int k, int p, 
     LR_CHECK_CUDA(cudaMemcpy2DAsync(oh.V.p, size_t(oh.V.ld) * 4, o.V.p, size_t(o.V.ld) * 4, size_t(a.n) * 4, size_t(k),
                                     cudaMemcpyDeviceToHost, c.s));
     LR_CHECK_CUDA(cudaMemcpyAsync(oh.S, o.S, sizeof(float) * k, cudaMemcpyDeviceToHost, c.s));
+  });
+}
+
+lr_status lr_subspace_iter_op(lr_handle h, const lr_operator* J, int k, int p, int v, const lr_mat* Omega, lr_mat* U,
+                              lr_mat* S, lr_mat* V, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    check_op(J);
+    AMat a;  // shapes only
+    a.m = J->rows;
+    a.n = J->cols;
+    a.ld = J->cols;
+    check_kpv(a, k, p, v, 2);
+    Mat om = check_thin(Omega, a.n, k + p, "Omega");
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    const Viewer vw = op_viewer(J, false);
+    run_subspace(c, a, k, k + p, v, om, o, &vw);
+  });
+}
+
+lr_status lr_nystrom_tevd(lr_handle h, const lr_operator* J, int k, int p, int v, const lr_mat* Omega, lr_mat* V,
+                          lr_mat* Lambda2, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    check_op(J);
+    AMat a;
+    a.m = J->rows;
+    a.n = J->cols;
+    check_kpv(a, k, p, v, 2);
+    LR_REQUIRE(k + p <= 128, LR_ERR_UNSUPPORTED, "lr_nystrom_tevd: k + p <= 128");
+    Mat om = check_thin(Omega, v % 2 == 0 ? a.n : a.m, k + p, "Omega");
+    Mat vo = check_thin(V, a.n, k, "V");
+    LR_REQUIRE(Lambda2 && Lambda2->data && Lambda2->dtype == LR_F32 && Lambda2->rows * Lambda2->cols >= k,
+               LR_ERR_SHAPE, "Lambda2 must hold k F32 values");
+    Ctx c = make_ctx(h, opts, stream);
+    run_nystrom(c, J, k, k + p, v, om, vo, static_cast<float*>(Lambda2->data));
+  });
+}
+
+lr_status lr_pinched_tevd(lr_handle h, const lr_operator* J, int k, int p, int v, const lr_mat* Omega, lr_mat* V,
+                          lr_mat* Lambda2, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    check_op(J);
+    AMat a;
+    a.m = J->rows;
+    a.n = J->cols;
+    check_kpv(a, k, p, v, 2);
+    Mat om = check_thin(Omega, v % 2 == 0 ? a.m : a.n, k + p, "Omega");
+    Mat vo = check_thin(V, a.n, k, "V");
+    LR_REQUIRE(Lambda2 && Lambda2->data && Lambda2->dtype == LR_F32 && Lambda2->rows * Lambda2->cols >= k,
+               LR_ERR_SHAPE, "Lambda2 must hold k F32 values");
+    Ctx c = make_ctx(h, opts, stream);
+    run_pinched(c, J, k, k + p, v, om, vo, static_cast<float*>(Lambda2->data));
   });
 }
 

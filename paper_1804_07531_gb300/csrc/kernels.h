@@ -111,6 +111,13 @@ void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd
 // run_if (device int, optional): zero only when *run_if != 0.
 void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s, const int* run_if = nullptr);
 void zero_bytes(void* p, size_t bytes, cudaStream_t s);
+// Normal-matrix TEVD helpers: *out = sum of squares (FP64); Y += nu Q and
+// out_i = max(S_i^2 - nu, 0) with nu = scale * sqrt(*sumsq); B = (B + B^T) / 2.
+void sumsq_f32(const float* Y, int64_t ld, int64_t rows, int64_t cols, double* out, cudaStream_t s);
+void shift_add_f32(float* Y, int64_t ldy, const float* Q, int64_t ldq, int64_t rows, int64_t cols, const double* sumsq,
+                   float scale, cudaStream_t s);
+void symmetrize_f64(double* B, int n, cudaStream_t s);
+void sq_shift(const float* S, int k, const double* sumsq, float scale, float* out, cudaStream_t s);
 // dst (bf16, col-major rows x cols, ldd) = round(src); with lo != nullptr
 // also lo = round(src - hi) (the hi/lo split of a thin operand).
 void f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, __nv_bfloat16* lo, int64_t ldd, int64_t rows,

@@ -408,6 +408,64 @@ void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s, 
   }
 }
 
+// ---- small helpers of the normal-matrix TEVDs (Alg. 4)
+__global__ void sumsq_kernel(const float* __restrict__ Y, int64_t ld, int64_t rows, int64_t cols, double* out) {
+  double acc = 0.0;
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x) {
+      const double y = Y[r + c * ld];
+      acc += y * y;
+    }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+// Y += nu Q with nu = scale * sqrt(*sumsq)
+__global__ void shift_add_kernel(float* __restrict__ Y, int64_t ldy, const float* __restrict__ Q, int64_t ldq,
+                                 int64_t rows, int64_t cols, const double* sumsq, float scale) {
+  const float nu = float(scale * sqrt(*sumsq));
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x)
+      Y[r + c * ldy] = fmaf(nu, Q[r + c * ldq], Y[r + c * ldy]);
+}
+__global__ void sym_f64_kernel(double* B, int n) {
+  const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (idx >= int64_t(n) * n) return;
+  const int i = int(idx % n), j = int(idx / n);
+  if (i < j) {
+    const double m = 0.5 * (B[i + int64_t(j) * n] + B[j + int64_t(i) * n]);
+    B[i + int64_t(j) * n] = m;
+    B[j + int64_t(i) * n] = m;
+  }
+}
+// out_i = max(S_i^2 - nu, 0) with nu = scale * sqrt(*sumsq) (or S_i^2 when sumsq is null)
+__global__ void sq_shift_kernel(const float* S, int k, const double* sumsq, float scale, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k) return;
+  const float nu = sumsq ? float(scale * sqrt(*sumsq)) : 0.f;
+  out[i] = fmaxf(S[i] * S[i] - nu, 0.f);
+}
+
+void sumsq_f32(const float* Y, int64_t ld, int64_t rows, int64_t cols, double* out, cudaStream_t s) {
+  LR_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+  if (rows <= 0 || cols <= 0) return;
+  sumsq_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(Y, ld, rows, cols, out);
+  LR_LAUNCH_CHECK();
+}
+void shift_add_f32(float* Y, int64_t ldy, const float* Q, int64_t ldq, int64_t rows, int64_t cols, const double* sumsq,
+                   float scale, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  shift_add_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(Y, ldy, Q, ldq, rows, cols, sumsq, scale);
+  LR_LAUNCH_CHECK();
+}
+void symmetrize_f64(double* B, int n, cudaStream_t s) {
+  sym_f64_kernel<<<grid_for(int64_t(n) * n), 256, 0, s>>>(B, n);
+  LR_LAUNCH_CHECK();
+}
+void sq_shift(const float* S, int k, const double* sumsq, float scale, float* out, cudaStream_t s) {
+  sq_shift_kernel<<<(k + 127) / 128, 128, 0, s>>>(S, k, sumsq, scale, out);
+  LR_LAUNCH_CHECK();
+}
+
 void zero_bytes(void* p, size_t bytes, cudaStream_t s) {
   if (bytes) LR_CHECK_CUDA(cudaMemsetAsync(p, 0, bytes, s));
 }
