@@ -265,6 +265,37 @@ lr_status lr_nystrom_tevd(lr_handle handle, const lr_operator* J, int k, int p, 
 lr_status lr_pinched_tevd(lr_handle handle, const lr_operator* J, int k, int p, int v, const lr_mat* Omega,
                           lr_mat* V, lr_mat* Lambda2, const lr_opts* opts, void* stream);
 
+/* Single-view TSVD, Woolfe variant (Alg. 8, Section 6.5): the sketches of
+ * lr_single_pass; Q_c and Q_r are the leading k + l_c left singular vectors
+ * of Y_c = A Omega and Y_r = A^T Psi (opts->l_c as in lr_single_pass, minus
+ * LR_LC_MINVAR), X^ the least-squares solution of (Psi^T Q_c) X^ =
+ * Y_r^T Q_r, U = Q_c U^ and V = Q_r V^ from the SVD of X^.  Arguments,
+ * outputs and errors as lr_single_pass; the workspace as lr_workspace_size
+ * with ell1, ell2. */
+lr_status lr_single_pass_woolfe(lr_handle handle, const lr_mat* A, int k, const lr_mat* Omega, const lr_mat* Psi,
+                                lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts, void* stream);
+
+/* Single-view TSVD with the extended sketch of Section 6.7 (the
+ * approximation bwz2): Y_c = A Omega, Y_r = A^T Psi and Z = Phi_r^T A Phi_c,
+ * all from one pass over A (A Phi_c rides in the range view with Omega);
+ * Q_c R_c = Y_c, Q_r R_r = Y_r, U_c T_c = Phi_r^T Q_c, U_r T_r = Phi_c^T Q_r,
+ * C = T_c^{-1} U_c^T Z U_r T_r^{-T}, U = Q_c U^, V = Q_r V^ from C's SVD.
+ * Omega n x ell, Psi m x ell (l_1 = l_2), Phi_c n x s and Phi_r m x s with
+ * ell <= s <= min(m, n) (F32 column-major; lr_srft forms SRFT ones).
+ * Outputs and errors as lr_single_pass.  The workspace needs
+ * lr_workspace_size(m, n, ell + s, ell + s, 1). */
+lr_status lr_single_pass_extended(lr_handle handle, const lr_mat* A, int k, const lr_mat* Omega, const lr_mat* Psi,
+                                  const lr_mat* Phi_c, const lr_mat* Phi_r, lr_mat* U, lr_mat* S, lr_mat* V,
+                                  const lr_opts* opts, void* stream);
+
+/* The SRFT test matrix of Section 6.7, Phi = D F P (n x s, F32 column-major,
+ * written into Phi on the device): D = diag(signs) (n Rademacher signs, F32
+ * +-1, device), F the orthonormal DCT-II matrix (columns the cosine basis:
+ * F[j, k] = c_k sqrt(2/n) cos(pi (2j+1) k / (2n)), c_0 = 1/sqrt(2), else 1),
+ * P the columns cols[0..s) (distinct indices in [0, n), device int32).
+ * Asynchronous on `stream`. */
+lr_status lr_srft(lr_handle handle, int64_t n, int s, const float* signs, const int* cols, lr_mat* Phi, void* stream);
+
 /* Reverse pass of lr_subspace_iter for the loss L = sum_i dS_i sigma_i
  * (dS: k weights, F32): writes dA = dL/dA (m x n, F32 row-major, same shape
  * as A, overwritten).  The forward views are recomputed, not stored.  A must

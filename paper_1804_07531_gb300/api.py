@@ -18,7 +18,8 @@ from ._binding import (APPLY_FN, Handle, LowrankError, LrMat, LrOperator, _opts,
 __all__ = [
     "sketch", "sketch_chained", "orth", "subspace_iter", "single_pass", "block_krylov",
     "rowwise_single_pass", "subspace_iter_backward", "single_pass_host", "subspace_iter_host", "block_krylov_host",
-    "Operator", "MatrixOperator", "subspace_iter_op", "nystrom_tevd", "pinched_tevd", "device_status",
+    "Operator", "MatrixOperator", "subspace_iter_op", "nystrom_tevd", "pinched_tevd", "single_pass_woolfe",
+    "single_pass_extended", "srft", "device_status",
     "LowrankError",
 ]
 
@@ -400,3 +401,51 @@ def pinched_tevd(op, k, p, v, omega, stream=None):
     """Alg. 5: (V, Lambda2), the pinched rank-k EVD of J^T J from v >= 2 views
     of J.  omega: rows x (k+p) for even v, cols x (k+p) for odd v."""
     return _tevd(lib().lr_pinched_tevd, op, k, p, v, omega, stream)
+
+
+
+# ------------------------------------------- other single-view methods
+def single_pass_woolfe(a, k, omega, psi, l_c=None, stream=None):
+    """Alg. 8 (Woolfe variant of the single view): (U, S, V)."""
+    a, (omega, psi) = _prep(a, omega, psi)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    h.reserve(m, n, omega.shape[1], psi.shape[1], 1)
+    u, s, vv = _outs(a, k)
+    mats = [mat_a(a), mat_thin(omega), mat_thin(psi), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts(l_c=l_c)
+    _call(h, lib().lr_single_pass_woolfe, _p(mats[0]), k, _p(mats[1]), _p(mats[2]), _p(mats[3]), _p(mats[4]),
+          _p(mats[5]), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+def srft(n, signs, cols, device=None, stream=None):
+    """Phi = D F P (n x s, column-major float32 on the device): D = diag(signs)
+    (+-1), F the orthonormal DCT-II matrix, P the columns `cols`."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    signs = torch.as_tensor(signs, dtype=torch.float32).to(dev).contiguous()
+    cols = torch.as_tensor(cols, dtype=torch.int32).to(dev).contiguous()
+    s = int(cols.numel())
+    phi = empty_cm(n, s, dev)
+    h = Handle.get(dev)
+    mp = mat_thin(phi)
+    h.check(lib().lr_srft(h.h, int(n), s, ctypes.c_void_p(signs.data_ptr()), ctypes.c_void_p(cols.data_ptr()),
+                          _p(mp), ctypes.c_void_p(_stream(stream))))
+    return phi
+
+
+def single_pass_extended(a, k, omega, psi, phi_c, phi_r, stream=None):
+    """Section 6.7 (bwz2): single view with the extended sketch Z = Phi_r^T A
+    Phi_c, e.g. with SRFT test matrices from srft(); (U, S, V)."""
+    a, (omega, psi, phi_c, phi_r) = _prep(a, omega, psi, phi_c, phi_r)
+    h = Handle.get(a.device)
+    m, n = a.shape
+    w = omega.shape[1] + phi_c.shape[1]
+    h.reserve(m, n, w, w, 1, extra=4 * (2 * (m + n) * w) + 1024)
+    u, s, vv = _outs(a, k)
+    mats = [mat_a(a), mat_thin(omega), mat_thin(psi), mat_thin(phi_c), mat_thin(phi_r), mat_thin(u), mat_thin(s),
+            mat_thin(vv)]
+    o = _opts()
+    _call(h, lib().lr_single_pass_extended, _p(mats[0]), k, *[_p(x) for x in mats[1:]], ctypes.byref(o),
+          ctypes.c_void_p(_stream(stream)))
+    return u, s, vv

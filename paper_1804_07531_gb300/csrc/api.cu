@@ -935,6 +935,122 @@ void run_single_pass(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const
   write_outputs(c, Qc, Vj, Xt, W, Lc, Sv, k, o);
 }
 
+// ------------------------------------------------------------ Alg. 8
+// Woolfe variant of the single view: Q_c and Q_r are the leading k + l_c
+// left singular vectors of both sketches, X^ the least-squares solution of
+// (Psi^T Q_c) X^ = Y_r^T Q_r (through the QR of Psi^T Q_c), U = Q_c U^,
+// V = Q_r V^ from the SVD of X^.
+void run_woolfe(Ctx& c, const AMat& A, int k, int l_c, const Mat& Om, const Mat& Psi, Outs& o) {
+  ArenaScope sc(c.ar);
+  const int ell1 = int(Om.cols), ell2 = int(Psi.cols), l1 = ell1 - k;
+  const int lc = (l_c < 0 || l_c > l1) ? l1 : l_c, kc = k + lc;
+  Mat Y{c.ar.take<float>(size_t(A.m) * ell1), A.m, ell1, A.m};
+  Mat Z{c.ar.take<float>(size_t(A.n) * ell2), A.n, ell2, A.n};
+  Mat Zq{c.ar.take<float>(size_t(A.n) * ell2), A.n, ell2, A.n};
+  Mat Qc{c.ar.take<float>(size_t(A.m) * kc), A.m, kc, A.m};
+  Mat Qr{c.ar.take<float>(size_t(A.n) * kc), A.n, kc, A.n};
+  double* Rc = c.ar.take<double>(size_t(ell1) * ell1);
+  double* Rr = c.ar.take<double>(size_t(ell2) * ell2);
+  float* Wc = c.ar.take<float>(size_t(ell1) * ell1);
+  float* Vc = c.ar.take<float>(size_t(ell1) * ell1);
+  float* Sc = c.ar.take<float>(size_t(ell1));
+  float* Wr = c.ar.take<float>(size_t(ell2) * ell2);
+  float* Vr = c.ar.take<float>(size_t(ell2) * ell2);
+  float* Sr = c.ar.take<float>(size_t(ell2));
+  double* P64 = c.ar.take<double>(size_t(ell2) * kc);
+  Mat P{c.ar.take<float>(size_t(ell2) * kc), ell2, kc, ell2};
+  float* Rhs = c.ar.take<float>(size_t(ell2) * kc);
+  double* Rh = c.ar.take<double>(size_t(kc) * kc);
+  float* Rhi = c.ar.take<float>(size_t(kc) * kc);
+  float* M1 = c.ar.take<float>(size_t(kc) * kc);
+  float* X = c.ar.take<float>(size_t(kc) * kc);
+  float* Ux = c.ar.take<float>(size_t(kc) * kc);
+  float* Vx = c.ar.take<float>(size_t(kc) * kc);
+  float* Sx = c.ar.take<float>(size_t(kc));
+  view_dual(c, A, Om, Y, Psi, Z);                  // Y_c = A Omega, Y_r = A^T Psi
+  if (c.measure) {
+    orth(c, Mat{nullptr, std::max(A.m, A.n), std::max(ell1, ell2), std::max(A.m, A.n)}, nullptr);
+    core_svd(c, nullptr, std::max(ell1, ell2), nullptr, nullptr, nullptr);
+    tri_inv_any(c, nullptr, kc, nullptr);
+    return;
+  }
+  copy_f32(Z.p, Z.ld, Zq.p, Zq.ld, A.n, ell2, c.s);
+  orth(c, Y, Rc);                                    // Y_c = Q_c R_c
+  core_svd(c, Rc, ell1, Wc, Vc, Sc);                 // leading left vectors of R_c
+  gemm(c, A.m, kc, ell1, false, Y.p, Y.ld, false, Wc, ell1, Qc.p, Qc.ld);
+  orth(c, Zq, Rr);                                   // Y_r = Q_r R_r
+  core_svd(c, Rr, ell2, Wr, Vr, Sr);
+  gemm(c, A.n, kc, ell2, false, Zq.p, Zq.ld, false, Wr, ell2, Qr.p, Qr.ld);
+  gram64(c, ell2, kc, A.m, Psi.p, Psi.ld, Qc.p, Qc.ld, P64, ell2);     // Psi^T Q_c
+  f64_to_f32(P64, ell2, P.p, P.ld, ell2, kc, c.s);
+  gram64(c, ell2, kc, A.n, Z.p, Z.ld, Qr.p, Qr.ld, P64, ell2);         // Y_r^T Q_r
+  f64_to_f32(P64, ell2, Rhs, ell2, ell2, kc, c.s);
+  orth(c, P, Rh);                                    // Psi^T Q_c = Q^ R^
+  gemm(c, kc, kc, ell2, true, P.p, P.ld, false, Rhs, ell2, M1, kc);   // Q^^T (Y_r^T Q_r)
+  tri_inv_any(c, Rh, kc, Rhi);
+  gemm(c, kc, kc, kc, false, Rhi, kc, false, M1, kc, X, kc);          // X^ = R^^{-1} Q^^T Y_r^T Q_r
+  jacobi_svd(X, kc, kc, kc, Ux, kc, Vx, kc, Sx, nullptr, c.status, c.s);
+  write_outputs(c, Qc, Ux, Qr, Vx, kc, Sx, k, o);
+}
+
+// ------------------------------------------------------- Section 6.7
+// The extended sketch with SRFT test matrices (the approximation bwz2):
+// Y_c = A Omega and A Phi_c from the same range view as Y_r = A^T Psi,
+// Z = Phi_r^T (A Phi_c), U_c T_c = Phi_r^T Q_c, U_r T_r = Phi_c^T Q_r,
+// C = T_c^{-1} U_c^T Z U_r T_r^{-T}, U = Q_c U^, V = Q_r V^ from C's SVD.
+void run_extended(Ctx& c, const AMat& A, int k, const Mat& Om, const Mat& Psi, const Mat& Phc, const Mat& Phr,
+                  Outs& o) {
+  ArenaScope sc(c.ar);
+  const int ell = int(Om.cols), s = int(Phc.cols), w = ell + s;
+  Mat Xc{c.ar.take<float>(size_t(A.n) * w), A.n, w, A.n};
+  Mat Yc{c.ar.take<float>(size_t(A.m) * w), A.m, w, A.m};
+  Mat Yr{c.ar.take<float>(size_t(A.n) * ell), A.n, ell, A.n};
+  double* G64 = c.ar.take<double>(size_t(s) * std::max(s, ell));
+  float* Zs = c.ar.take<float>(size_t(s) * s);
+  Mat Bc{c.ar.take<float>(size_t(s) * ell), s, ell, s};
+  Mat Br{c.ar.take<float>(size_t(s) * ell), s, ell, s};
+  double* Tc = c.ar.take<double>(size_t(ell) * ell);
+  double* Tr = c.ar.take<double>(size_t(ell) * ell);
+  float* Tci = c.ar.take<float>(size_t(ell) * ell);
+  float* Tri = c.ar.take<float>(size_t(ell) * ell);
+  float* M1 = c.ar.take<float>(size_t(ell) * s);
+  float* M2 = c.ar.take<float>(size_t(ell) * ell);
+  float* C1 = c.ar.take<float>(size_t(ell) * ell);
+  float* Cm = c.ar.take<float>(size_t(ell) * ell);
+  float* Uc = c.ar.take<float>(size_t(ell) * ell);
+  float* Vc = c.ar.take<float>(size_t(ell) * ell);
+  float* Sc = c.ar.take<float>(size_t(ell));
+  Mat Y{Yc.p, A.m, ell, A.m};
+  Mat W{Yc.p + size_t(A.m) * ell, A.m, s, A.m};
+  if (c.measure) {
+    view_dual(c, A, Xc, Yc, Psi, Yr);
+    orth(c, Mat{nullptr, std::max(A.m, A.n), ell, std::max(A.m, A.n)}, nullptr);
+    tri_inv_any(c, nullptr, ell, nullptr);
+    return;
+  }
+  copy_f32(Om.p, Om.ld, Xc.p, Xc.ld, A.n, ell, c.s);
+  copy_f32(Phc.p, Phc.ld, Xc.p + size_t(A.n) * ell, Xc.ld, A.n, s, c.s);
+  view_dual(c, A, Xc, Yc, Psi, Yr);                 // [A Omega, A Phi_c] and A^T Psi, one pass
+  gram64(c, s, s, A.m, Phr.p, Phr.ld, W.p, W.ld, G64, s);   // Z = Phi_r^T (A Phi_c)
+  f64_to_f32(G64, s, Zs, s, s, s, c.s);
+  orth(c, Y, nullptr);                               // Q_c
+  orth(c, Yr, nullptr);                              // Q_r
+  gram64(c, s, ell, A.m, Phr.p, Phr.ld, Y.p, Y.ld, G64, s);    // Phi_r^T Q_c
+  f64_to_f32(G64, s, Bc.p, Bc.ld, s, ell, c.s);
+  orth(c, Bc, Tc);                                   // U_c T_c
+  gram64(c, s, ell, A.n, Phc.p, Phc.ld, Yr.p, Yr.ld, G64, s);  // Phi_c^T Q_r
+  f64_to_f32(G64, s, Br.p, Br.ld, s, ell, c.s);
+  orth(c, Br, Tr);                                   // U_r T_r
+  gemm(c, ell, s, s, true, Bc.p, Bc.ld, false, Zs, s, M1, ell);         // U_c^T Z
+  gemm(c, ell, ell, s, false, M1, ell, false, Br.p, Br.ld, M2, ell);    // (.) U_r
+  tri_inv_any(c, Tc, ell, Tci);
+  tri_inv_any(c, Tr, ell, Tri);
+  gemm(c, ell, ell, ell, false, Tci, ell, false, M2, ell, C1, ell);     // T_c^{-1} (.)
+  gemm(c, ell, ell, ell, false, C1, ell, true, Tri, ell, Cm, ell);      // (.) T_r^{-T}
+  jacobi_svd(Cm, ell, ell, ell, Uc, ell, Vc, ell, Sc, nullptr, c.status, c.s);
+  write_outputs(c, Y, Uc, Yr, Vc, ell, Sc, k, o);
+}
+
 // ------------------------------------------------- reverse of Alg. 2
 // dA for L = sum_i dS_i sigma_i(R) where R is the last view's triangular
 // factor (the core of Alg. 2).  The forward views are recomputed (nothing is
@@ -1301,6 +1417,10 @@ lr_status lr_workspace_size(lr_handle h, int64_t m, int64_t n, int ell1, int ell
       measure([&](Ctx& c) { run_krylov(c, A, k, ell1, vv, Om, o); });
       measure([&](Ctx& c) { run_krylov_rowwise(c, A, k, ell1, vv, Om, o); });
       measure([&](Ctx& c) { run_rowwise_qb(c, A, k, ell1, Om, o); });
+      if (ell2 >= ell1) {
+        Mat Ps{nullptr, m, ell2, m};
+        measure([&](Ctx& c) { run_woolfe(c, A, std::max(1, ell1 - 1), -1, Om, Ps, o); });
+      }
       if (!A.bf16 && ell1 <= 128) {  // the operator forms (shapes only: no callback in measuring mode)
         lr_operator op{m, n, nullptr, nullptr};
         measure([&](Ctx& c) { run_nystrom(c, &op, k, ell1, vv, Om, Mat{nullptr, n, k, n}, nullptr); });
@@ -1601,6 +1721,51 @@ lr_status lr_pinched_tevd(lr_handle h, const lr_operator* J, int k, int p, int v
                LR_ERR_SHAPE, "Lambda2 must hold k F32 values");
     Ctx c = make_ctx(h, opts, stream);
     run_pinched(c, J, k, k + p, v, om, vo, static_cast<float*>(Lambda2->data));
+  });
+}
+
+lr_status lr_single_pass_woolfe(lr_handle h, const lr_mat* A, int k, const lr_mat* Omega, const lr_mat* Psi,
+                                lr_mat* U, lr_mat* S, lr_mat* V, const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    LR_REQUIRE(Omega && Psi, LR_ERR_INVALID_ARG, "Omega and Psi are required");
+    Mat om = check_thin(Omega, a.n, -1, "Omega");
+    Mat ps = check_thin(Psi, a.m, -1, "Psi");
+    LR_REQUIRE(k >= 1 && om.cols > k, LR_ERR_INVALID_ARG, "need ell1 > k");
+    LR_REQUIRE(ps.cols >= om.cols, LR_ERR_INVALID_ARG, "need ell2 >= ell1 (l_2 >= l_1)");
+    LR_REQUIRE(ps.cols <= std::min(a.m, a.n), LR_ERR_INVALID_ARG, "ell2 larger than min(m, n)");
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    run_woolfe(c, a, k, opts ? opts->l_c : -1, om, ps, o);
+  });
+}
+
+lr_status lr_single_pass_extended(lr_handle h, const lr_mat* A, int k, const lr_mat* Omega, const lr_mat* Psi,
+                                  const lr_mat* Phi_c, const lr_mat* Phi_r, lr_mat* U, lr_mat* S, lr_mat* V,
+                                  const lr_opts* opts, void* stream) {
+  return guarded(h, [&] {
+    AMat a = check_A(A);
+    LR_REQUIRE(Omega && Psi && Phi_c && Phi_r, LR_ERR_INVALID_ARG, "Omega, Psi, Phi_c and Phi_r are required");
+    Mat om = check_thin(Omega, a.n, -1, "Omega");
+    Mat ps = check_thin(Psi, a.m, om.cols, "Psi");
+    Mat pc = check_thin(Phi_c, a.n, -1, "Phi_c");
+    Mat pr = check_thin(Phi_r, a.m, pc.cols, "Phi_r");
+    LR_REQUIRE(k >= 1 && om.cols > k, LR_ERR_INVALID_ARG, "need ell > k");
+    LR_REQUIRE(pc.cols >= om.cols, LR_ERR_INVALID_ARG, "need s >= ell");
+    LR_REQUIRE(pc.cols <= std::min(a.m, a.n), LR_ERR_INVALID_ARG, "s larger than min(m, n)");
+    Outs o = check_outs(a, k, U, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    run_extended(c, a, k, om, ps, pc, pr, o);
+  });
+}
+
+lr_status lr_srft(lr_handle h, int64_t n, int s, const float* signs, const int* cols, lr_mat* Phi, void* stream) {
+  return guarded(h, [&] {
+    LR_REQUIRE(signs && cols, LR_ERR_INVALID_ARG, "signs and cols are required");
+    LR_REQUIRE(n >= 1 && s >= 1 && s <= n, LR_ERR_SHAPE, "need 1 <= s <= n");
+    Mat phi = check_thin(Phi, n, s, "Phi");
+    Ctx c = make_ctx(h, nullptr, stream);
+    srft(n, s, signs, cols, phi.p, phi.ld, c.s);
   });
 }
 

@@ -111,6 +111,9 @@ void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd
 // run_if (device int, optional): zero only when *run_if != 0.
 void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s, const int* run_if = nullptr);
 void zero_bytes(void* p, size_t bytes, cudaStream_t s);
+// SRFT test matrix Phi = D F P (n x s): Rademacher signs (F32 +-1, n), DCT-II
+// columns cols (s distinct indices in [0, n)).
+void srft(int64_t n, int s, const float* signs, const int* cols, float* phi, int64_t ld, cudaStream_t st);
 // Normal-matrix TEVD helpers: *out = sum of squares (FP64); Y += nu Q and
 // out_i = max(S_i^2 - nu, 0) with nu = scale * sqrt(*sumsq); B = (B + B^T) / 2.
 void sumsq_f32(const float* Y, int64_t ld, int64_t rows, int64_t cols, double* out, cudaStream_t s);

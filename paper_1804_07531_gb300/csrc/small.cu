@@ -466,6 +466,29 @@ void sq_shift(const float* S, int k, const double* sumsq, float scale, float* ou
   LR_LAUNCH_CHECK();
 }
 
+// Phi = D F P (n x s, column-major): Phi[j, t] = signs[j] c_k sqrt(2 / n)
+// cos(pi (2j + 1) k / (2n)) with k = cols[t] (c_0 = 1 / sqrt(2), else 1).  The
+// phase (2j + 1) k is reduced modulo 4n in integers, so cospif sees an
+// argument below 2 whatever n and k are.
+__global__ void srft_kernel(int64_t n, int s, const float* __restrict__ signs, const int* __restrict__ cols,
+                            float* __restrict__ phi, int64_t ld) {
+  const float base = sqrtf(2.f / float(n));
+  for (int t = blockIdx.y; t < s; t += gridDim.y) {
+    const int64_t k = cols[t];
+    const float scale = k == 0 ? base * 0.70710678118654752f : base;
+    for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+      const int64_t ph = ((2 * j + 1) * k) % (4 * n);
+      phi[j + int64_t(t) * ld] = signs[j] * scale * cospif(float(ph) / float(2 * n));
+    }
+  }
+}
+
+void srft(int64_t n, int s, const float* signs, const int* cols, float* phi, int64_t ld, cudaStream_t st) {
+  if (n <= 0 || s <= 0) return;
+  srft_kernel<<<grid_2d(n, s), 256, 0, st>>>(n, s, signs, cols, phi, ld);
+  LR_LAUNCH_CHECK();
+}
+
 void zero_bytes(void* p, size_t bytes, cudaStream_t s) {
   if (bytes) LR_CHECK_CUDA(cudaMemsetAsync(p, 0, bytes, s));
 }
