@@ -348,6 +348,9 @@ def workload_c4(dev, reps=10):
     ds = torch.ones(k, device=dev)
     ms_f = _timed(lambda: api.subspace_iter(a, k, p, v, om), reps)
     ms_b = _timed(lambda: api.subspace_iter_backward(a, k, p, v, om, ds), reps)
+    du = torch.randn(m, k, generator=gen, device=dev)
+    dv = torch.randn(n, k, generator=gen, device=dev)
+    ms_buv = _timed(lambda: api.subspace_iter_backward(a, k, p, v, om, ds=ds, du=du, dv=dv), reps)
     st = api.device_status(dev.index or 0)
     a64 = a.double().cpu().numpy()
     om64 = om.double().cpu().numpy()
@@ -357,6 +360,7 @@ def workload_c4(dev, reps=10):
     return {"workload": "grad_subspace_v4_f32_8192x4096_k32_p8", "status": st,
             "forward_ms": round(ms_f, 4), "backward_ms": round(ms_b, 4),
             "forward_plus_backward_ms": round(ms_f + ms_b, 4),
+            "backward_u_s_v_ms": round(ms_buv, 4),
             "cpu_oracle_forward_s": round(t_orc, 3), "cpu_oracle_cores": _threads()}
 
 

@@ -304,6 +304,18 @@ lr_status lr_subspace_iter_backward(lr_handle handle, const lr_mat* A, int k, in
                                     const lr_mat* Omega, const lr_mat* dS, lr_mat* dA,
                                     const lr_opts* opts, void* stream);
 
+/* Reverse pass of lr_subspace_iter for a loss on all three outputs,
+ * L = <dU, U> + <dS, S> + <dV, V> (the gradients of any loss at the
+ * outputs): writes dA = dL/dA.  dU (m x k) and dV (n x k) are F32
+ * column-major, dS k F32 values; any of the three may be NULL (zero), not
+ * all.  The reverse of the core SVD couples the k kept singular pairs to the
+ * other ell - k of the core through 1 / (s_j^2 - s_i^2) (a pair whose two
+ * values coincide contributes nothing), and the sign fix of the forward is
+ * applied to dU and dV.  Otherwise as lr_subspace_iter_backward. */
+lr_status lr_subspace_iter_backward_uv(lr_handle handle, const lr_mat* A, int k, int p, int v, const lr_mat* Omega,
+                                       const lr_mat* dU, const lr_mat* dS, const lr_mat* dV, lr_mat* dA,
+                                       const lr_opts* opts, void* stream);
+
 /* ---------------------------------------------------------------------
  * Instrumentation (the paper has no counterpart; used by benchmarks).
  * ------------------------------------------------------------------- */

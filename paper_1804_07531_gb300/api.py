@@ -177,18 +177,29 @@ def selftest_bounded_wait(timeout_us=20000, device=None, stream=None) -> int:
     return h.status(stream)
 
 
-def subspace_iter_backward(a, k, p, v, omega, ds, stream=None):
-    """dA for L = sum_i ds_i sigma_i of Alg. 2 (views recomputed, dA written once)."""
+def subspace_iter_backward(a, k, p, v, omega, ds=None, du=None, dv=None, stream=None):
+    """dA for L = <du, U> + <ds, S> + <dv, V> of Alg. 2 (views recomputed, dA
+    written once); any of du, ds, dv may be None (zero), not all."""
     a, (omega,) = _prep(a, omega)
     h = Handle.get(a.device)
     m, n = a.shape
     h.reserve(m, n, k + p, 0, v)
-    ds = ds.detach().to(device=a.device, dtype=torch.float32).contiguous()
     da = torch.empty(m, n, device=a.device, dtype=torch.float32)
-    mats = [mat_a(a), mat_thin(omega), mat_thin(ds), mat_a(da)]
+    keep = []
+
+    def opt_mat(t, thin=True):
+        if t is None:
+            return None
+        t = col_major(t.detach().to(device=a.device, dtype=torch.float32)) if thin else \
+            t.detach().to(device=a.device, dtype=torch.float32).contiguous()
+        mt = mat_thin(t)
+        keep.append((t, mt))
+        return _p(mt)
+
+    mA, mom, mda = mat_a(a), mat_thin(omega), mat_a(da)
     o = _opts()
-    _call(h, lib().lr_subspace_iter_backward, _p(mats[0]), k, p, v, _p(mats[1]), _p(mats[2]), _p(mats[3]),
-          ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
+    _call(h, lib().lr_subspace_iter_backward_uv, _p(mA), k, p, v, _p(mom), opt_mat(du), opt_mat(ds, thin=False),
+          opt_mat(dv), _p(mda), ctypes.byref(o), ctypes.c_void_p(_stream(stream)))
     return da
 
 

@@ -1062,8 +1062,8 @@ void run_extended(Ctx& c, const AMat& A, int k, const Mat& Om, const Mat& Psi, c
 // Every dA term is an outer product of two ell-column panels, so dA is
 // written once by one GEMM: dA = [L_1 .. L_v] [R_1 .. R_v]^T with
 // (L_j, R_j) = (Bb_j, X_j) for odd j and (X_j, Bb_j) for even j.
-void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, const float* dS, float* dA,
-                           int64_t ldda) {
+void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, const float* dS,
+                           const Mat* dU, const Mat* dV, float* dA, int64_t ldda) {
   ArenaScope sc(c.ar);
   const int64_t m = A.m, n = A.n;
   Mat Lc{c.ar.take<float>(size_t(m) * v * ell), m, int64_t(v) * ell, m};   // m-side panels
@@ -1084,6 +1084,19 @@ void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const M
   float* rhs = c.ar.take<float>(size_t(mx) * ell);
   float* Qb = c.ar.take<float>(size_t(mx) * ell);
   float* dSd = c.ar.take<float>(size_t(ell));
+  // gradients on U and V: [dU; dV] with the forward's sign fix applied, the
+  // unfixed U, W^T Wb and Z^T Zb, the middle factor, and the lift term of
+  // the second-to-last view's Q
+  const int64_t mn = m + n;
+  float* DD = c.ar.take<float>(size_t(mn) * k);
+  float* Ur = c.ar.take<float>(size_t(m) * k);
+  double* X64 = c.ar.take<double>(size_t(ell) * k);
+  float* dUh = c.ar.take<float>(size_t(ell) * k);
+  float* dVh = c.ar.take<float>(size_t(ell) * k);
+  float* Xw = c.ar.take<float>(size_t(ell) * k);
+  float* Xz = c.ar.take<float>(size_t(ell) * k);
+  float* Inner = c.ar.take<float>(size_t(ell) * ell);
+  float* Qp = c.ar.take<float>(size_t(mx) * ell);
   // slot j (1-based) of the panel lists; Q_j of view j lands in the slot of
   // view j + 1 (odd j: Lc, even j: Rc), Omega in Rc slot 1
   auto lslot = [&](int j) { return Mat{Lc.col(int64_t(j - 1) * ell), m, ell, m}; };
@@ -1105,13 +1118,51 @@ void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const M
     else view_corange(c, A, in, out);
     orth(c, out, Rs + size_t(j - 1) * ell * ell);
   }
-  // ---- core: R_v = W S Z^T, Rb = W_k diag(dS) Z_k^T
+  // ---- core: R_v = W S Z^T
   core_svd(c, Rs + size_t(v - 1) * ell * ell, ell, W, Z, Sv);
-  LR_CHECK_CUDA(cudaMemcpyAsync(dSd, dS, sizeof(float) * k, cudaMemcpyDeviceToDevice, c.s));
-  scale_cols_f32(W, ell, ell, k, dSd, c.s);
-  gemm(c, ell, ell, k, false, W, ell, true, Z, ell, Rb, ell);
-  // ---- reverse through the views
+  const bool uv = dU != nullptr || dV != nullptr;
   bool have_qb = false;
+  if (!uv) {
+    // sigma only: Rb = W_k diag(dS) Z_k^T
+    LR_CHECK_CUDA(cudaMemcpyAsync(dSd, dS, sizeof(float) * k, cudaMemcpyDeviceToDevice, c.s));
+    scale_cols_f32(W, ell, ell, k, dSd, c.s);
+    gemm(c, ell, ell, k, false, W, ell, true, Z, ell, Rb, ell);
+  } else {
+    // Outputs (as the forward forms them): v odd R_c = U^ L V^^T, U = Q_v U^_k,
+    // V = Q_{v-1} V^_k; v even R_r = V^ L U^^T, U = Q_{v-1} U^_k, V = Q_v V^_k.
+    const bool vodd = v % 2 == 1;
+    Mat Qprev = vodd ? rslot(v) : lslot(v);            // Q_{v-1} sits in view v's slot
+    const Mat Qc = vodd ? Qv : Qprev, Qr = vodd ? Qprev : Qv;
+    const float* Uh = vodd ? W : Z;
+    const float* Vh = vodd ? Z : W;
+    // [dU; dV] with the sign flips of the forward's fix (decided on U = Q_c U^_k)
+    LR_CHECK_CUDA(cudaMemsetAsync(DD, 0, sizeof(float) * size_t(mn) * k, c.s));
+    if (dU) copy_f32(dU->p, dU->ld, DD, mn, m, k, c.s);
+    if (dV) copy_f32(dV->p, dV->ld, DD + m, mn, n, k, c.s);
+    gemm(c, m, k, ell, false, Qc.p, Qc.ld, false, Uh, ell, Ur, m);
+    fix_signs(Ur, m, m, DD, mn, mn, k, c.s);
+    const float* dUr = DD;
+    const float* dVr = DD + m;
+    // U^b = Q_c^T dU, V^b = Q_r^T dV; lift terms Q_c b = dU U^_k^T, Q_r b = dV V^_k^T
+    gram64(c, ell, k, m, Qc.p, Qc.ld, dUr, mn, X64, ell);
+    f64_to_f32(X64, ell, dUh, ell, ell, k, c.s);
+    gram64(c, ell, k, n, Qr.p, Qr.ld, dVr, mn, X64, ell);
+    f64_to_f32(X64, ell, dVh, ell, ell, k, c.s);
+    float* q_last = Qb;  // the lift term of Q_v starts the reverse pass
+    float* q_prev = Qp;
+    gemm(c, m, ell, k, false, dUr, mn, true, Uh, ell, vodd ? q_last : q_prev, m);
+    gemm(c, n, ell, k, false, dVr, mn, true, Vh, ell, vodd ? q_prev : q_last, n);
+    // the core's left factor carries U^ (v odd) or V^ (v even)
+    const float* Wb = vodd ? dUh : dVh;
+    const float* Zb = vodd ? dVh : dUh;
+    gemm(c, ell, k, ell, true, W, ell, false, Wb, ell, Xw, ell);   // W^T Wb
+    gemm(c, ell, k, ell, true, Z, ell, false, Zb, ell, Xz, ell);   // Z^T Zb
+    svd_bwd_inner(ell, k, Sv, dS, Xw, Xz, Inner, c.s);
+    gemm(c, ell, ell, ell, false, W, ell, false, Inner, ell, Mm, ell);
+    gemm(c, ell, ell, ell, false, Mm, ell, true, Z, ell, Rb, ell);  // Rb = W inner Z^T
+    have_qb = true;
+  }
+  // ---- reverse through the views
   for (int j = v; j >= 1; --j) {
     const bool odd = j % 2 == 1;
     const int64_t rows = odd ? m : n;
@@ -1138,6 +1189,7 @@ void run_subspace_backward(Ctx& c, const AMat& A, int k, int ell, int v, const M
       Mat qb{Qb, odd ? n : m, ell, odd ? n : m};
       if (odd) view_corange(c, A, Bb, qb);
       else view_range(c, A, Bb, qb);
+      if (uv && j == v) add_f32(Qb, qb.ld, Qp, qb.ld, qb.rows, ell, c.s);  // Q_{v-1}'s lift term
       have_qb = true;
     }
   }
@@ -1426,7 +1478,7 @@ lr_status lr_workspace_size(lr_handle h, int64_t m, int64_t n, int ell1, int ell
         measure([&](Ctx& c) { run_nystrom(c, &op, k, ell1, vv, Om, Mat{nullptr, n, k, n}, nullptr); });
         measure([&](Ctx& c) { run_pinched(c, &op, k, ell1, vv, Om, Mat{nullptr, n, k, n}, nullptr); });
       }
-      if (!A.bf16) measure([&](Ctx& c) { run_subspace_backward(c, A, 1, ell1, vv, Om, nullptr, nullptr, 0); });
+      if (!A.bf16) measure([&](Ctx& c) { run_subspace_backward(c, A, ell1, ell1, vv, Om, nullptr, nullptr, nullptr, nullptr, 0); });  // k <= ell
       if (ell2 >= ell1) {
         Mat Ps{nullptr, m, ell2, m};
         measure([&](Ctx& c) { run_single_pass(c, A, std::max(1, ell1 - 1), -1, Om, Ps, o); });
@@ -1769,22 +1821,33 @@ lr_status lr_srft(lr_handle h, int64_t n, int s, const float* signs, const int* 
   });
 }
 
-lr_status lr_subspace_iter_backward(lr_handle h, const lr_mat* A, int k, int p, int v, const lr_mat* Omega,
-                                    const lr_mat* dS, lr_mat* dA, const lr_opts* opts, void* stream) {
+lr_status lr_subspace_iter_backward_uv(lr_handle h, const lr_mat* A, int k, int p, int v, const lr_mat* Omega,
+                                       const lr_mat* dU, const lr_mat* dS, const lr_mat* dV, lr_mat* dA,
+                                       const lr_opts* opts, void* stream) {
   return guarded(h, [&] {
     AMat a = check_A(A);
     LR_REQUIRE(!a.bf16, LR_ERR_DTYPE, "the reverse pass needs an F32 A");
     check_kpv(a, k, p, v, 2);
     Mat om = check_thin(Omega, a.n, k + p, "Omega");
-    LR_REQUIRE(dS && dS->data && dS->dtype == LR_F32 && dS->rows * dS->cols >= k, LR_ERR_SHAPE,
+    LR_REQUIRE(dU || dS || dV, LR_ERR_INVALID_ARG, "need at least one of dU, dS, dV");
+    LR_REQUIRE(!dS || (dS->data && dS->dtype == LR_F32 && dS->rows * dS->cols >= k), LR_ERR_SHAPE,
                "dS must hold k F32 weights");
+    Mat du, dv;
+    if (dU) du = check_thin(dU, a.m, k, "dU");
+    if (dV) dv = check_thin(dV, a.n, k, "dV");
     LR_REQUIRE(dA && dA->data && dA->dtype == LR_F32 && dA->col_major == 0 && dA->rows == a.m && dA->cols == a.n &&
                    dA->ld >= a.n,
                LR_ERR_SHAPE, "dA must be an F32 row-major m x n matrix");
     Ctx c = make_ctx(h, opts, stream);
-    run_subspace_backward(c, a, k, k + p, v, om, static_cast<const float*>(dS->data), static_cast<float*>(dA->data),
-                          dA->ld);
+    run_subspace_backward(c, a, k, k + p, v, om, dS ? static_cast<const float*>(dS->data) : nullptr,
+                          dU ? &du : nullptr, dV ? &dv : nullptr, static_cast<float*>(dA->data), dA->ld);
   });
+}
+
+lr_status lr_subspace_iter_backward(lr_handle h, const lr_mat* A, int k, int p, int v, const lr_mat* Omega,
+                                    const lr_mat* dS, lr_mat* dA, const lr_opts* opts, void* stream) {
+  if (!dS) return h ? LR_ERR_INVALID_ARG : LR_ERR_INVALID_ARG;
+  return lr_subspace_iter_backward_uv(h, A, k, p, v, Omega, nullptr, dS, nullptr, dA, opts, stream);
 }
 
 lr_status lr_set_trace(lr_handle h, int on) {

@@ -111,6 +111,12 @@ void split_tf32(const float* src, int64_t lds, float* hi, float* lo, int64_t ldd
 // run_if (device int, optional): zero only when *run_if != 0.
 void zero_f32(float* p, int64_t rows, int64_t cols, int64_t ld, cudaStream_t s, const int* run_if = nullptr);
 void zero_bytes(void* p, size_t bytes, cudaStream_t s);
+// Reverse of a square SVD: the middle factor of Rb = W inner Z^T from
+// Xw = W^T Wb, Xz = Z^T Zb (ell x k; either may be null) and dS (k; may be null).
+void svd_bwd_inner(int ell, int k, const float* S, const float* dS, const float* Xw, const float* Xz, float* inner,
+                   cudaStream_t s);
+// Y += X (rows x cols, column-major).
+void add_f32(float* Y, int64_t ldy, const float* X, int64_t ldx, int64_t rows, int64_t cols, cudaStream_t s);
 // SRFT test matrix Phi = D F P (n x s): Rademacher signs (F32 +-1, n), DCT-II
 // columns cols (s distinct indices in [0, n)).
 void srft(int64_t n, int s, const float* signs, const int* cols, float* phi, int64_t ld, cudaStream_t st);

@@ -489,6 +489,50 @@ void srft(int64_t n, int s, const float* signs, const int* cols, float* phi, int
   LR_LAUNCH_CHECK();
 }
 
+// Reverse of a square SVD R = W diag(s) Z^T (full, distinct s) for
+// gradients on the k kept pairs: with Xw = W^T Wb and Xz = Z^T Zb (ell x k,
+// the columns past k of Wb, Zb being zero), the middle factor of
+// Rb = W inner Z^T is inner_ij = F_ij ((Xw_ij - Xw_ji) s_j + s_i (Xz_ij - Xz_ji))
+// for i != j, F_ij = 1 / (s_j^2 - s_i^2) (0 where the two coincide), and
+// inner_ii = dS_i (i < k).
+__global__ void svd_bwd_inner_kernel(int ell, int k, const float* __restrict__ S, const float* __restrict__ dS,
+                                     const float* __restrict__ Xw, const float* __restrict__ Xz, float* inner) {
+  const int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (idx >= int64_t(ell) * ell) return;
+  const int i = int(idx % ell), j = int(idx / ell);
+  float v = 0.f;
+  if (i == j) {
+    v = (dS && i < k) ? dS[i] : 0.f;
+  } else {
+    const float xw_ij = (Xw && j < k) ? Xw[i + int64_t(j) * ell] : 0.f;
+    const float xw_ji = (Xw && i < k) ? Xw[j + int64_t(i) * ell] : 0.f;
+    const float xz_ij = (Xz && j < k) ? Xz[i + int64_t(j) * ell] : 0.f;
+    const float xz_ji = (Xz && i < k) ? Xz[j + int64_t(i) * ell] : 0.f;
+    const float si = S[i], sj = S[j];
+    const float d = sj * sj - si * si;
+    const float f = fabsf(d) > 1e-30f ? 1.f / d : 0.f;
+    v = f * ((xw_ij - xw_ji) * sj + si * (xz_ij - xz_ji));
+  }
+  inner[idx] = v;
+}
+__global__ void add_f32_kernel(float* __restrict__ Y, int64_t ldy, const float* __restrict__ X, int64_t ldx,
+                               int64_t rows, int64_t cols) {
+  for (int64_t c = blockIdx.y; c < cols; c += gridDim.y)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows; r += int64_t(gridDim.x) * blockDim.x)
+      Y[r + c * ldy] += X[r + c * ldx];
+}
+
+void svd_bwd_inner(int ell, int k, const float* S, const float* dS, const float* Xw, const float* Xz, float* inner,
+                   cudaStream_t s) {
+  svd_bwd_inner_kernel<<<grid_for(int64_t(ell) * ell), 256, 0, s>>>(ell, k, S, dS, Xw, Xz, inner);
+  LR_LAUNCH_CHECK();
+}
+void add_f32(float* Y, int64_t ldy, const float* X, int64_t ldx, int64_t rows, int64_t cols, cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return;
+  add_f32_kernel<<<grid_2d(rows, cols), 256, 0, s>>>(Y, ldy, X, ldx, rows, cols);
+  LR_LAUNCH_CHECK();
+}
+
 void zero_bytes(void* p, size_t bytes, cudaStream_t s) {
   if (bytes) LR_CHECK_CUDA(cudaMemsetAsync(p, 0, bytes, s));
 }

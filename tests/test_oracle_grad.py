@@ -62,3 +62,52 @@ def test_grad_approaches_exact_top_k_gradient():
     g = G.grad_topk_sigma_sum(a, om, k, 6)
     exact = u[:, :k] @ vv[:, :k].T
     assert np.linalg.norm(g - exact) / np.linalg.norm(exact) < 1e-3
+
+
+def test_svd_backward_matches_finite_differences():
+    n = 8
+    r = np.triu(S.gaussian(n, n, seed=61)) + np.diag(np.arange(n, 0, -1.0))
+    wb, sb, zb = S.gaussian(n, n, seed=62), S.gaussian(n, 1, seed=63)[:, 0], S.gaussian(n, n, seed=64)
+
+    def f(rr):
+        w, s, z = L.jacobi_svd(rr)
+        # the sign of each singular pair is fixed by w's largest entry, as the library does
+        idx = np.argmax(np.abs(w), axis=0)
+        d = np.sign(w[idx, np.arange(n)])
+        return float(np.sum(w * d * wb) + s @ sb + np.sum(z * d * zb))
+
+    w, s, z = L.jacobi_svd(r)
+    idx = np.argmax(np.abs(w), axis=0)
+    d = np.sign(w[idx, np.arange(n)])
+    g = G.svd_backward(w, s, z, wb * d, sb, zb * d)
+    for sd in range(6):
+        e = S.gaussian(n, n, seed=70 + sd)
+        h = 1e-6
+        fd = (f(r + h * e) - f(r - h * e)) / (2 * h)
+        assert abs(fd - np.sum(g * e)) < 1e-6 * max(1.0, abs(fd)), (sd, fd, np.sum(g * e))
+
+
+@pytest.mark.parametrize("v", [2, 3, 4])
+def test_grad_through_u_s_v_matches_finite_differences(v):
+    """L = <Ub, U> + <Sb, S> + <Vb, V> of Alg. 2's outputs: the reverse pass
+    against central differences along 12 seeded directions."""
+    m, n, k, ell = 60, 45, 5, 10
+    a, _ = _gap_matrix(m, n, 81)
+    a = a + 1e-3 * S.gaussian(m, n, seed=82)
+    om = S.gaussian(n, ell, seed=83)
+    ub, sb, vb = S.gaussian(m, k, seed=84), S.gaussian(k, 1, seed=85)[:, 0], S.gaussian(n, k, seed=86)
+
+    def f(aa):
+        u, s, vv = G.lowrank_outputs(aa, om, k, v)
+        return float(np.sum(u * ub) + s @ sb + np.sum(vv * vb))
+
+    g = G.grad_lowrank(a, om, k, v, ub, sb, vb)
+    h = 1e-6 * np.abs(a).max()
+    for sd in range(12):
+        e = S.gaussian(m, n, seed=200 + sd)
+        fd = (f(a + h * e) - f(a - h * e)) / (2 * h)
+        an = float(np.sum(g * e))
+        assert abs(fd - an) <= 2e-6 * max(1.0, abs(an)), (sd, fd, an)
+    # with Ub = Vb = 0 it is the singular-value gradient of before
+    g0 = G.grad_lowrank(a, om, k, v, None, np.ones(k), None)
+    assert np.max(np.abs(g0 - G.grad_topk_sigma_sum(a, om, k, v))) < 1e-12 * np.abs(g0).max()
