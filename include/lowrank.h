@@ -296,6 +296,39 @@ lr_status lr_single_pass_extended(lr_handle handle, const lr_mat* A, int k, cons
  * Asynchronous on `stream`. */
 lr_status lr_srft(lr_handle handle, int64_t n, int s, const float* signs, const int* cols, lr_mat* Phi, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Row-sharded matrices over several GPUs (one process per GPU).
+ * ------------------------------------------------------------------- */
+
+/* The caller's collective: allreduce(ctx, buf, count, dtype, stream) sums
+ * `count` elements of the device array buf (dtype LR_F32 or LR_F64) over
+ * all ranks, in place, ordered on `stream` (e.g. an NCCL all-reduce on that
+ * stream); returns 0 on success.  Every rank calls it the same number of
+ * times with the same counts, in the same order. */
+typedef int (*lr_allreduce_fn)(void* ctx, void* buf, int64_t count, int dtype, void* stream);
+typedef struct {
+  int rank, world;
+  lr_allreduce_fn allreduce;
+  void* ctx;
+} lr_comm;
+
+/* Alg. 2 on a matrix whose rows are split over the ranks: rank g holds A_g
+ * (m_g x n, the g-th block of rows, any m_g >= 1) and the same Omega
+ * (n x (k+p)); it receives U_g (m_g x k, its rows of U), and S and V
+ * (replicated).  Range views A_g X are local; each co-range view sums
+ * A_g^T W_g over the ranks (one all-reduce of n x (k+p) F32); the thin QR
+ * of the row-sharded Q_c all-reduces its (k+p) x (k+p) FP64 Grams (and the
+ * block projections) and factors the sum on every rank; the replicated
+ * factors (Q_r and R_r, the core SVD) are taken from rank 0 (an all-reduce
+ * with zeros elsewhere), so every rank holds the same bits; the sign of each
+ * pair is fixed by the largest-magnitude entry of u_i over all ranks (ties
+ * to the lowest global row), as in lr_subspace_iter.  Requires
+ * k + p <= min(sum m_g, n); the caller checks that the ranks agree on the
+ * shapes and arguments.  Otherwise as lr_subspace_iter. */
+lr_status lr_subspace_iter_sharded(lr_handle handle, const lr_mat* A_local, int k, int p, int v, const lr_mat* Omega,
+                                   lr_mat* U_local, lr_mat* S, lr_mat* V, const lr_comm* comm, const lr_opts* opts,
+                                   void* stream);
+
 /* Reverse pass of lr_subspace_iter for the loss L = sum_i dS_i sigma_i
  * (dS: k weights, F32): writes dA = dL/dA (m x n, F32 row-major, same shape
  * as A, overwritten).  The forward views are recomputed, not stored.  A must

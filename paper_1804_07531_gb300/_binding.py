@@ -31,7 +31,8 @@ EXPORTS = [
     "lr_set_workspace", "lr_get_status", "lr_sketch", "lr_sketch_chained", "lr_orth",
     "lr_subspace_iter", "lr_single_pass", "lr_block_krylov", "lr_rowwise_single_pass",
     "lr_single_pass_host", "lr_subspace_iter_host", "lr_block_krylov_host", "lr_subspace_iter_op",
-    "lr_nystrom_tevd", "lr_pinched_tevd", "lr_single_pass_woolfe", "lr_single_pass_extended", "lr_srft", "lr_subspace_iter_backward", "lr_subspace_iter_backward_uv", "lr_set_trace", "lr_trace_read",
+    "lr_nystrom_tevd", "lr_pinched_tevd", "lr_single_pass_woolfe", "lr_single_pass_extended", "lr_srft", "lr_subspace_iter_backward",
+    "lr_subspace_iter_backward_uv", "lr_subspace_iter_sharded", "lr_set_trace", "lr_trace_read",
     "lr_kernel_launches", "lr_sketch_range_static", "lr_sketch_range_static_status", "lr_selftest_bounded_wait",
 ]
 TRACE_KINDS = {"view_range": 0, "view_corange": 1, "orth": 2, "core_svd": 3, "view_dual": 4}
@@ -56,6 +57,16 @@ APPLY_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.
 
 class LrOperator(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("apply", APPLY_FN), ("ctx", ctypes.c_void_p)]
+
+
+# int allreduce(void* ctx, void* buf, int64_t count, int dtype, void* stream)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                ctypes.c_void_p)
+
+
+class LrComm(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int), ("world", ctypes.c_int), ("allreduce", ALLREDUCE_FN),
+                ("ctx", ctypes.c_void_p)]
 
 
 class LowrankError(RuntimeError):
@@ -109,6 +120,7 @@ def lib():
             L.lr_srft.argtypes = [P, I64, I, P, P, M, P]
             L.lr_subspace_iter_backward.argtypes = [P, M, I, I, I, M, M, M, O, P]
             L.lr_subspace_iter_backward_uv.argtypes = [P, M, I, I, I, M, M, M, M, M, O, P]
+            L.lr_subspace_iter_sharded.argtypes = [P, M, I, I, I, M, M, M, M, ctypes.POINTER(LrComm), O, P]
             L.lr_set_trace.argtypes = [P, I]
             L.lr_trace_read.argtypes = [P, I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64), I]
             L.lr_kernel_launches.argtypes = [P, ctypes.POINTER(ctypes.c_uint64)]

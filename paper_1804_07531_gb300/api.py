@@ -12,10 +12,11 @@ import ctypes
 
 import torch
 
-from ._binding import (APPLY_FN, Handle, LowrankError, LrMat, LrOperator, _opts, _stream, col_major, empty_cm, lib,
-                       mat_a, mat_thin)
+from ._binding import (ALLREDUCE_FN, APPLY_FN, Handle, LowrankError, LrComm, LrMat, LrOperator, _opts, _stream,
+                       col_major, empty_cm, lib, mat_a, mat_thin)
 
 __all__ = [
+    "Comm", "TorchDistComm", "subspace_iter_sharded",
     "sketch", "sketch_chained", "orth", "subspace_iter", "single_pass", "block_krylov",
     "rowwise_single_pass", "subspace_iter_backward", "single_pass_host", "subspace_iter_host", "block_krylov_host",
     "Operator", "MatrixOperator", "subspace_iter_op", "nystrom_tevd", "pinched_tevd", "single_pass_woolfe",
@@ -459,4 +460,87 @@ def single_pass_extended(a, k, omega, psi, phi_c, phi_r, stream=None):
     o = _opts()
     _call(h, lib().lr_single_pass_extended, _p(mats[0]), k, *[_p(x) for x in mats[1:]], ctypes.byref(o),
           ctypes.c_void_p(_stream(stream)))
+    return u, s, vv
+
+
+# ------------------------------------------------ rows over several GPUs
+def _wrap_buffer(ptr, count, dtype, device):
+    """A 1-D tensor over the library's buffer (float32 for dtype 0, float64
+    for dtype 2): device memory through __cuda_array_interface__, host
+    memory through ctypes."""
+    if dtype not in (0, 2):
+        raise ValueError(f"unsupported all-reduce dtype {dtype}")
+    if device.type == "cuda":
+        class _Buf:
+            __cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f4" if dtype == 0 else "<f8",
+                                        "data": (int(ptr), False), "strides": None, "version": 2}
+        return torch.as_tensor(_Buf(), device=device)
+    ctype = ctypes.c_float if dtype == 0 else ctypes.c_double
+    arr = (ctype * int(count)).from_address(int(ptr))
+    return torch.frombuffer(arr, dtype=torch.float32 if dtype == 0 else torch.float64)
+
+
+class Comm:
+    """The collective of the row-sharded entry points: this process's rank,
+    the number of ranks, and allreduce(t), which sums the 1-D tensor t
+    (float32 or float64, on `device`) over the ranks in place, ordered on
+    the current stream (the library's stream while it runs)."""
+
+    def __init__(self, rank, world, allreduce, device=None):
+        self.rank, self.world = int(rank), int(world)
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        self._allreduce = allreduce
+        self.error = None
+
+        def cb(ctx, buf, count, dtype, stream):
+            try:
+                t = _wrap_buffer(buf, count, dtype, self.device)
+                if self.device.type == "cuda":
+                    st = (torch.cuda.ExternalStream(stream, device=self.device) if stream
+                          else torch.cuda.default_stream(self.device))
+                    with torch.cuda.stream(st):
+                        self._allreduce(t)
+                else:
+                    self._allreduce(t)
+                return 0
+            except Exception as e:  # reported to the caller by the entry point's status
+                self.error = e
+                return 1
+
+        self._cb = ALLREDUCE_FN(cb)
+        self.c = LrComm(self.rank, self.world, self._cb, None)
+
+
+class TorchDistComm(Comm):
+    """Comm over a torch.distributed process group (NCCL for device buffers;
+    gloo serves host buffers)."""
+
+    def __init__(self, group=None, device=None):
+        import torch.distributed as dist
+        super().__init__(dist.get_rank(group), dist.get_world_size(group),
+                         lambda t: dist.all_reduce(t, group=group), device)
+
+
+def subspace_iter_sharded(a_local, k, p, v, omega, comm, shifted_fallback=False, split_last=False, handle=None,
+                          stream=None):
+    """Alg. 2 on a matrix whose rows are split over comm.world ranks: this
+    rank holds a_local (its block of rows, in rank order) and the common
+    omega (n x (k + p)); returns (U_local, S, V) -- its rows of U, and S and
+    V, the same on every rank."""
+    a, (omega,) = _prep(a_local, omega)
+    h = handle if handle is not None else Handle.get(a.device)
+    m, n = a.shape
+    h.reserve(m, n, k + p, 0, v)
+    u, s, vv = _outs(a, k)
+    mats = [mat_a(a), mat_thin(omega), mat_thin(u), mat_thin(s), mat_thin(vv)]
+    o = _opts(shifted_fallback=shifted_fallback, split_last=split_last)
+    comm.error = None
+    st = lib().lr_subspace_iter_sharded(h.h, _p(mats[0]), k, p, v, _p(mats[1]), _p(mats[2]), _p(mats[3]),
+                                        _p(mats[4]), ctypes.byref(comm.c), ctypes.byref(o),
+                                        ctypes.c_void_p(_stream(stream)))
+    if st != 0 and comm.error is not None:
+        raise comm.error
+    h.check(st)
     return u, s, vv

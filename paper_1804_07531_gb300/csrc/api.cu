@@ -62,7 +62,22 @@ struct Ctx {
   int* status = nullptr;
   lr_opts opt{};
   bool measure = false;
+  const lr_comm* comm = nullptr;  // row-sharded runs: the caller's all-reduce
 };
+
+// Sum a device buffer over the ranks (no-op without a communicator).
+void allreduce(Ctx& c, void* buf, int64_t count, lr_dtype dt) {
+  if (c.measure || !c.comm || c.comm->world <= 1 || count <= 0) return;
+  const int rc = c.comm->allreduce(c.comm->ctx, buf, count, int(dt), c.s);
+  LR_REQUIRE(rc == 0, LR_ERR_INVALID_ARG, "the communicator's all-reduce failed (returned " + std::to_string(rc) + ")");
+}
+// Every rank takes rank 0's copy of a replicated buffer.
+void broadcast0(Ctx& c, void* buf, int64_t count, lr_dtype dt) {
+  if (c.measure || !c.comm || c.comm->world <= 1 || count <= 0) return;
+  if (c.comm->rank != 0)
+    LR_CHECK_CUDA(cudaMemsetAsync(buf, 0, size_t(count) * (dt == LR_F64 ? 8 : 4), c.s));
+  allreduce(c, buf, count, dt);
+}
 
 // Records a begin/end event pair around a traced region (no-op unless the
 // handle traces and events remain in the pool).
@@ -412,9 +427,10 @@ void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
 // QR, as the first block of a Krylov basis is); they are kept as they are
 // and only the remaining columns are projected and factorised (R must then
 // be null).
-void orth(Ctx& c, Mat Y, double* R, int done = 0) {
+void orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
   const int64_t m = Y.rows;
-  LR_REQUIRE(m >= Y.cols, LR_ERR_SHAPE, "orth needs rows >= cols");
+  // sharded: Y holds this rank's rows; the caller checks the total
+  LR_REQUIRE(sharded || m >= Y.cols, LR_ERR_SHAPE, "orth needs rows >= cols");
   LR_REQUIRE(done == 0 || R == nullptr, LR_ERR_INVALID_ARG, "orth: R is not formed for kept columns");
   const int L = int(Y.cols) - done;
   if (L <= 0) return;
@@ -439,6 +455,7 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0) {
     if (c0 > 0) {
       for (int pass = 0; pass < 2; ++pass) {
         gram64(c, c0, w, m, Y.p, Y.ld, Yb, Y.ld, G64, c0);          // C = Q_prev^T Y_b
+        if (sharded) allreduce(c, G64, int64_t(c0) * w, LR_F64);    // rows split over the ranks
         f64_to_f32(G64, c0, C32, c0, c0, w, c.s);
         gemm(c, m, w, c0, false, Y.p, Y.ld, false, C32, c0, Yb, Y.ld, -1.f, 1.f);  // Y_b -= Q_prev C
         if (R) add_block_f64(R, L, 0, c0, G64, c0, c0, w, c.s);
@@ -459,22 +476,26 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0) {
     double* Rbb = R ? R + c0 + int64_t(c0) * L : nullptr;
     // pass 1: Y_b -> T
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w);
+    if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
     chol_inv(G64, w, Rinv, w, Rbb, L, true, CHOL_SHIFT_IF_NEEDED, more, c.status, c.s);
     gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m);
     // pass 2: T -> Y_b (R_bb <- R_2 R_bb by a separate many-CTA product)
     gram64(c, w, w, m, T, m, T, m, G64, w);
+    if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
     chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, robust ? CHOL_SHIFT_IF_FLAGGED : CHOL_PLAIN, more,
              c.status, c.s);
     if (Rbb) upper_product(R2, w, Rbb, L, w, nullptr, c.s);
     gemm(c, m, w, w, false, T, m, false, Rinv, w, Yb, Y.ld);
     // pass 3 (only after a shifted pass 1): Y_b -> T -> Y_b
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w, more);
+    if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
     chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_IF_FLAGGED, more, c.status, c.s);
     if (Rbb) upper_product(R2, w, Rbb, L, w, more, c.s);
     gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m, 1.f, 0.f, more);
     if (robust) {
       // pass 4: T -> Y_b
       gram64(c, w, w, m, T, m, T, m, G64, w, more);
+      if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
       chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_IF_FLAGGED, more, c.status, c.s);
       if (Rbb) upper_product(R2, w, Rbb, L, w, more, c.s);
       gemm(c, m, w, w, false, T, m, false, Rinv, w, Yb, Y.ld, 1.f, 0.f, more);
@@ -587,6 +608,86 @@ void run_subspace(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, O
     core_svd(c, Rc, ell, W, Vj, Sv);
     write_outputs(c, Qc, W, Qr, Vj, ell, Sv, k, o);
   }
+}
+
+// ------------------------------------------------ Alg. 2, rows over ranks
+// Rank g holds the row block A_g; Q_c is split by rows like A, Q_r (n x ell)
+// is replicated.  Range views and every product with Q_c are local; the
+// thin QR of Q_c sums its Grams over the ranks (orth's sharded form: the
+// sums are identical on every rank, so is each Cholesky factor); a co-range
+// view sums the partials A_g^T Q_c,g.  The replicated results of kernels
+// that reduce with atomics (the thin QR of Q_r, the product for V) and the
+// core SVD are then taken from rank 0, so every rank holds the same bits.
+// The sign rule looks at the peak entry of each u_i over all ranks.
+void run_subspace_sharded(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o) {
+  ArenaScope sc(c.ar);
+  const int64_t n = A.n;
+  Mat Qc{c.ar.take<float>(size_t(A.m) * ell), A.m, ell, A.m};
+  Mat Qr{c.ar.take<float>(size_t(n) * ell), n, ell, n};
+  float* Vt = c.ar.take<float>(size_t(n) * k);
+  double* Rc = c.ar.take<double>(size_t(ell) * ell);
+  double* Rr = c.ar.take<double>(size_t(ell) * ell);
+  float* W = c.ar.take<float>(size_t(ell) * ell);
+  float* Vj = c.ar.take<float>(size_t(ell) * ell);
+  float* Sv = c.ar.take<float>(size_t(ell));
+  Mat cur = Om;
+  for (int j = 1; j <= v; ++j) {
+    if (j % 2 == 1) {
+      view_range(c, A, cur, Qc, j == v);           // A_g Q_r
+      orth(c, Qc, Rc, 0, true);                    // [Q_c, R_c] = qr(A Q_r), Grams summed
+    } else {
+      view_corange(c, A, Qc, Qr, j == v);          // A_g^T Q_c,g
+      allreduce(c, Qr.p, n * ell, LR_F32);         // A^T Q_c = sum_g A_g^T Q_c,g
+      orth(c, Qr, Rr);                             // [Q_r, R_r] = qr(A^T Q_c)
+      broadcast0(c, Qr.p, n * ell, LR_F32);
+      broadcast0(c, Rr, int64_t(ell) * ell, LR_F64);
+      cur = Qr;
+    }
+  }
+  core_svd(c, v % 2 == 0 ? Rr : Rc, ell, W, Vj, Sv);
+  if (c.measure) return;
+  broadcast0(c, W, int64_t(ell) * ell, LR_F32);
+  broadcast0(c, Vj, int64_t(ell) * ell, LR_F32);
+  broadcast0(c, Sv, ell, LR_F32);
+  // v even: R_r = V^ L U^^T (U from the right vectors); v odd: R_c = U^ L V^^T
+  const float* Lsel = v % 2 == 0 ? Vj : W;
+  const float* Rsel = v % 2 == 0 ? W : Vj;
+  gemm(c, o.U.rows, k, ell, false, Qc.p, Qc.ld, false, Lsel, ell, o.U.p, o.U.ld);
+  gemm(c, n, k, ell, false, Qr.p, Qr.ld, false, Rsel, ell, Vt, n);
+  broadcast0(c, Vt, n * k, LR_F32);
+  // Q_r is dead now: its storage holds the world x k peak entries (world <= n)
+  const int world = c.comm ? c.comm->world : 1, rank = c.comm ? c.comm->rank : 0;
+  float* peaks = Qr.p;
+  LR_CHECK_CUDA(cudaMemsetAsync(peaks, 0, sizeof(float) * size_t(world) * k, c.s));
+  col_peaks(o.U.p, o.U.ld, o.U.rows, peaks, rank, k, c.s);
+  allreduce(c, peaks, int64_t(world) * k, LR_F32);
+  flip_by_peaks(o.U.p, o.U.ld, o.U.rows, Vt, n, n, peaks, world, k, c.s);
+  copy_f32(Vt, n, o.V.p, o.V.ld, n, k, c.s);
+  LR_CHECK_CUDA(cudaMemcpyAsync(o.S, Sv, sizeof(float) * k, cudaMemcpyDeviceToDevice, c.s));
+}
+
+// The ranks agree on n, k, p, v and A's type (sum_g x_g = W x and
+// sum_g x_g^2 = W x^2 hold for the local x only when every x_g equals it);
+// returns the total row count.
+int64_t sharded_agree(Ctx& c, const AMat& A, int k, int p, int v) {
+  ArenaScope sc(c.ar);
+  double* d = c.ar.take<double>(16);
+  const double x[5] = {double(A.n), double(k), double(p), double(v), A.bf16 ? 1.0 : 0.0};
+  double h[12] = {double(A.m), 1.0};
+  for (int i = 0; i < 5; ++i) {
+    h[2 + 2 * i] = x[i];
+    h[3 + 2 * i] = x[i] * x[i];
+  }
+  LR_CHECK_CUDA(cudaMemcpyAsync(d, h, sizeof(h), cudaMemcpyHostToDevice, c.s));
+  allreduce(c, d, 12, LR_F64);
+  LR_CHECK_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c.s));
+  LR_CHECK_CUDA(cudaStreamSynchronize(c.s));
+  const double W = double(c.comm->world);
+  LR_REQUIRE(h[1] == W, LR_ERR_INVALID_ARG, "the communicator's all-reduce does not sum over comm->world ranks");
+  for (int i = 0; i < 5; ++i)
+    LR_REQUIRE(h[2 + 2 * i] == W * x[i] && h[3 + 2 * i] == W * x[i] * x[i], LR_ERR_INVALID_ARG,
+               "the ranks disagree on n, k, p, v or the type of A");
+  return int64_t(h[0]);
 }
 
 // ---------------------------------------------------- Algs. 3, 4, 5
@@ -1466,6 +1567,7 @@ lr_status lr_workspace_size(lr_handle h, int64_t m, int64_t n, int ell1, int ell
       Outs o;
       const int k = 1;
       measure([&](Ctx& c) { run_subspace(c, A, k, ell1, vv, Om, o); });
+      measure([&](Ctx& c) { run_subspace_sharded(c, A, ell1, ell1, vv, Om, o); });  // (m = the local rows)
       measure([&](Ctx& c) { run_krylov(c, A, k, ell1, vv, Om, o); });
       measure([&](Ctx& c) { run_krylov_rowwise(c, A, k, ell1, vv, Om, o); });
       measure([&](Ctx& c) { run_rowwise_qb(c, A, k, ell1, Om, o); });
@@ -1553,6 +1655,26 @@ lr_status lr_subspace_iter(lr_handle h, const lr_mat* A, int k, int p, int v, co
     Outs o = check_outs(a, k, U, S, V);
     Ctx c = make_ctx(h, opts, stream);
     run_subspace(c, a, k, k + p, v, om, o);
+  });
+}
+
+lr_status lr_subspace_iter_sharded(lr_handle h, const lr_mat* A_local, int k, int p, int v, const lr_mat* Omega,
+                                   lr_mat* U_local, lr_mat* S, lr_mat* V, const lr_comm* comm, const lr_opts* opts,
+                                   void* stream) {
+  return guarded(h, [&] {
+    LR_REQUIRE(comm && comm->allreduce && comm->world >= 1 && comm->rank >= 0 && comm->rank < comm->world,
+               LR_ERR_INVALID_ARG, "bad communicator");
+    AMat a = check_A(A_local);
+    LR_REQUIRE(k >= 1 && p >= 0 && v >= 2, LR_ERR_INVALID_ARG, "need k >= 1, p >= 0 and v >= 2");
+    LR_REQUIRE(k + p <= a.n, LR_ERR_INVALID_ARG, "need k + p <= n");
+    LR_REQUIRE(comm->world <= a.n, LR_ERR_INVALID_ARG, "at most n ranks");
+    Mat om = check_thin(Omega, a.n, k + p, "Omega");
+    Outs o = check_outs(a, k, U_local, S, V);
+    Ctx c = make_ctx(h, opts, stream);
+    c.comm = comm;
+    const int64_t m = sharded_agree(c, a, k, p, v);
+    LR_REQUIRE(k + p <= m, LR_ERR_INVALID_ARG, "need k + p <= the total number of rows");
+    run_subspace_sharded(c, a, k, k + p, v, om, o);
   });
 }
 

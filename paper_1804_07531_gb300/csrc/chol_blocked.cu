@@ -405,7 +405,7 @@ size_t smem_for(int n) {
 void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int mode,
               int* needs_more, int* status, cudaStream_t s) {
   LR_REQUIRE(ell >= 1 && ell <= kMaxN, LR_ERR_UNSUPPORTED, "chol_inv: block width must be <= 128");
-  static bool attr[64] = {};
+  static std::atomic<bool> attr[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   if (!attr[dev & 63]) {
@@ -419,7 +419,7 @@ void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int 
 
 void tri_inv(const double* R, int ldr, int n, float* X, int ldx, int* status, cudaStream_t s) {
   LR_REQUIRE(n >= 1 && n <= kMaxN, LR_ERR_UNSUPPORTED, "tri_inv: n must be <= 128");
-  static bool attr[64] = {};
+  static std::atomic<bool> attr[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   if (!attr[dev & 63]) {

@@ -336,7 +336,7 @@ void launch_dual(const CUtensorMap& ma, const CUtensorMap& mx, const CUtensorMap
                  cudaStream_t s) {
   using C = DCfg<NCY, NH>;
   auto kern = dual_bf16_kernel<NCY, NH>;
-  static bool attr_set[64] = {};
+  static std::atomic<bool> attr_set[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   if (!attr_set[dev & 63]) {

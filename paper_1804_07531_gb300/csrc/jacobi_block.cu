@@ -587,13 +587,13 @@ void set_attrs(KernelFn f) {
 // exchanges but make V <- V J the longer path, measured slower), else at
 // most 32, that fits and whose cluster the device can place; 0 if none.
 int jacobi_block_size(int n) {
-  static int cache[64][1025] = {};  // per device and n; -1: none
+  static std::atomic<int> cache[64][1025];  // per device and n; 0: not yet known, -1: none
   if (n < 2 || n > 1024) return 0;
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
-  int& c = cache[dev & 63][n];
-  if (c != 0) return c > 0 ? c : 0;
-  c = -1;
+  const int known = cache[dev & 63][n].load();
+  if (known != 0) return known > 0 ? known : 0;
+  int c = -1;
   for (int i = 0; i < 10; ++i) {
     const int P = 1 << (i % 5);
     const BGeo g(n, P);
@@ -612,6 +612,7 @@ int jacobi_block_size(int n) {
       break;
     }
   }
+  cache[dev & 63][n].store(c);
   return c > 0 ? c : 0;
 }
 

@@ -295,7 +295,7 @@ size_t cluster_smem(int n, int P) { return Geo(n, P).floats * sizeof(float) + 64
 template <int G>
 void launch(int P, size_t smem, cudaStream_t s, const float* M, int ldm, int n, float* U, int ldu, float* V, int ldv,
             float* S, int* status) {
-  static bool attr[64] = {};
+  static std::atomic<bool> attr[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   if (!attr[dev & 63]) {

@@ -134,8 +134,16 @@ void f32_to_bf16(const float* src, int64_t lds, __nv_bfloat16* dst, __nv_bfloat1
 // run_if (device int, optional): skip the copy when *run_if == 0.
 void copy_f32(const float* src, int64_t lds, float* dst, int64_t ldd, int64_t rows, int64_t cols, cudaStream_t s,
               const int* run_if = nullptr);
-// dst row-major = src^T for an F32 col-major src (rows x cols) -> (cols x rows)
+// The sign rule of the outputs: flip (u_i, v_i), i < k, when the
+// largest-magnitude entry of u_i (lowest row on ties) is negative.
 void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n, int k, cudaStream_t s);
+// Rows of U split over ranks: the signed largest-magnitude entry of each
+// column into peaks[slot * k + col]; after the caller sums the world x k
+// buffer over the ranks, flip_by_peaks applies the sign rule of fix_signs
+// with the peak taken over all ranks (lowest rank on ties).
+void col_peaks(const float* U, int64_t ldu, int64_t m, float* peaks, int slot, int k, cudaStream_t s);
+void flip_by_peaks(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n, const float* peaks,
+                   int world, int k, cudaStream_t s);
 
 // ---------------------------------------------------- small dense kernels
 // Cholesky of an FP64-accumulated Gram (ell <= 128) in one CTA:

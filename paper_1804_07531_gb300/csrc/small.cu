@@ -45,10 +45,9 @@ __device__ __forceinline__ void take_max(float a, int64_t r, float& best, int64_
     bidx = r;
   }
 }
-__global__ void __launch_bounds__(1024) fix_signs_kernel(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv,
-                                                         int64_t n) {
-  const int col = blockIdx.x;
-  float* u = U + col * ldu;
+// The row of the largest-magnitude entry of u (m entries; lowest row on
+// ties; 0 when m == 0).  Called by every thread of the block.
+__device__ int64_t col_absmax_row(const float* u, int64_t m) {
   float best = -1.f;
   int64_t bidx = 0;
   const bool vec = (reinterpret_cast<uintptr_t>(u) & 15) == 0;
@@ -85,17 +84,55 @@ __global__ void __launch_bounds__(1024) fix_signs_kernel(float* U, int64_t ldu, 
     if (l == 0) si[0] = bidx;
   }
   __syncthreads();
-  const bool flip = u[si[0]] < 0.f;
-  __syncthreads();
-  if (!flip) return;
+  const int64_t r = si[0];
+  __syncthreads();  // si is reused by the next call
+  return r;
+}
+
+__device__ void negate_pair(float* u, int64_t m, float* v, int64_t n) {
+  const bool vec = (reinterpret_cast<uintptr_t>(u) & 15) == 0;
+  const int64_t m4 = vec ? m / 4 : 0;
   float4* w4 = reinterpret_cast<float4*>(u);
   for (int64_t q = threadIdx.x; q < m4; q += blockDim.x) {
     const float4 x = w4[q];
     w4[q] = make_float4(-x.x, -x.y, -x.z, -x.w);
   }
   for (int64_t r = 4 * m4 + threadIdx.x; r < m; r += blockDim.x) u[r] = -u[r];
-  float* v = V + col * ldv;
   for (int64_t r = threadIdx.x; r < n; r += blockDim.x) v[r] = -v[r];
+}
+
+__global__ void __launch_bounds__(1024) fix_signs_kernel(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv,
+                                                         int64_t n) {
+  const int col = blockIdx.x;
+  float* u = U + col * ldu;
+  const int64_t r = col_absmax_row(u, m);
+  if (u[r] < 0.f) negate_pair(u, m, V + col * ldv, n);
+}
+
+// Rows of U split over ranks: rank `slot` writes the signed peak entry of
+// each of its columns to peaks[slot * k + col] (the caller zeroes the
+// buffer; a sum over the ranks then holds every rank's peak).
+__global__ void __launch_bounds__(1024) col_peak_kernel(const float* U, int64_t ldu, int64_t m, float* peaks,
+                                                        int slot, int k) {
+  const int col = blockIdx.x;
+  const float* u = U + col * ldu;
+  const int64_t r = col_absmax_row(u, m);
+  if (threadIdx.x == 0) peaks[int64_t(slot) * k + col] = m > 0 ? u[r] : 0.f;
+}
+
+// The global peak of column col is the largest |peaks[g * k + col]| (the
+// lowest rank on ties, i.e. the lowest global row); (u_col, v_col) flips
+// when it is negative.
+__global__ void __launch_bounds__(1024) flip_by_peak_kernel(float* U, int64_t ldu, int64_t m, float* V,
+                                                            int64_t ldv, int64_t n, const float* peaks, int world,
+                                                            int k) {
+  const int col = blockIdx.x;
+  float best = -1.f, val = 0.f;
+  for (int g = 0; g < world; ++g) {
+    const float x = peaks[int64_t(g) * k + col];
+    if (fabsf(x) > best) { best = fabsf(x); val = x; }
+  }
+  if (val < 0.f) negate_pair(U + col * ldu, m, V + col * ldv, n);
 }
 
 // Upper-triangular inverse of R (n x n, column-major FP32 in smem, lda n):
@@ -557,6 +594,19 @@ void fix_signs(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t 
   LR_LAUNCH_CHECK();
 }
 
+void col_peaks(const float* U, int64_t ldu, int64_t m, float* peaks, int slot, int k, cudaStream_t s) {
+  if (k <= 0) return;
+  col_peak_kernel<<<k, 1024, 0, s>>>(U, ldu, m, peaks, slot, k);
+  LR_LAUNCH_CHECK();
+}
+
+void flip_by_peaks(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int64_t n, const float* peaks,
+                   int world, int k, cudaStream_t s) {
+  if (k <= 0) return;
+  flip_by_peak_kernel<<<k, 1024, 0, s>>>(U, ldu, m, V, ldv, n, peaks, world, k);
+  LR_LAUNCH_CHECK();
+}
+
 void add_block_f64(double* R, int ldr, int r0, int c0, const double* C, int ldc, int rows, int cols, cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return;
   add_block_kernel<<<grid_for(int64_t(rows) * cols), 256, 0, s>>>(R, ldr, r0, c0, C, ldc, rows, cols);
@@ -603,7 +653,7 @@ void jacobi_svd(float* M, int ldm, int rows, int cols, float* Wk, int ldw, float
     return;
   }
   if (need <= cap) {
-    static bool attr[64] = {};
+    static std::atomic<bool> attr[64];  // attributes set, per device
     if (!attr[dev & 63]) {
       LR_CHECK_CUDA(cudaFuncSetAttribute(jacobi_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(cap)));
       attr[dev & 63] = true;
@@ -617,11 +667,16 @@ void jacobi_svd(float* M, int ldm, int rows, int cols, float* Wk, int ldw, float
 }
 
 DevInfo dev_info(int device) {
-  static DevInfo cache[64];
-  DevInfo& d = cache[device & 63];
-  if (d.sms == 0) {
+  // filled once per device; concurrent first calls both query and store the same values
+  static std::atomic<int> sms[64], smem[64];
+  DevInfo d;
+  d.sms = sms[device & 63].load();
+  d.max_smem_optin = smem[device & 63].load();
+  if (d.sms == 0 || d.max_smem_optin == 0) {
     LR_CHECK_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, device));
     LR_CHECK_CUDA(cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    smem[device & 63].store(d.max_smem_optin);
+    sms[device & 63].store(d.sms);
   }
   return d;
 }

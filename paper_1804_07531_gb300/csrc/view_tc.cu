@@ -562,7 +562,7 @@ void launch_ncol(const CUtensorMap& ma, const CUtensorMap& mb, ViewParams p, int
   constexpr int STAGES = (NCOL <= 128) ? 4 : 3;
   using C = Cfg<MODE, NS, NCOL, STAGES>;
   auto kern = view_bf16_kernel<MODE, NS, NCOL, STAGES>;
-  static bool attr_set[64] = {};
+  static std::atomic<bool> attr_set[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   if (!attr_set[dev & 63]) {
@@ -632,7 +632,7 @@ void launch_tf32(const CUtensorMap& ma, const CUtensorMap& mbh, const CUtensorMa
   constexpr int STAGES = (NCOL <= 64) ? 4 : (NCOL <= 128) ? 3 : 2;
   using C = CfgT<MODE, NCOL, STAGES>;
   auto kern = view_tf32x3_kernel<MODE, NCOL, STAGES, SPLITB, OUT64>;
-  static bool attr_set[64] = {};
+  static std::atomic<bool> attr_set[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   if (!attr_set[dev & 63]) {
