@@ -443,6 +443,7 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
   float* Rinv = c.ar.take<float>(size_t(wmax) * wmax);
   double* R2 = c.ar.take<double>(size_t(wmax) * wmax);  // factor of a later pass
   int* flags = c.ar.take<int>(size_t(nb));
+  double* tscratch = c.ar.take<double>(orth_tc_scratch_doubles(wmax));
   if (c.measure) return;
   TraceScope tr(c, LR_TRACE_ORTH);
   if (R) LR_CHECK_CUDA(cudaMemsetAsync(R, 0, size_t(L) * L * sizeof(double), c.s));
@@ -474,6 +475,12 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
     // Passes alternate Y_b -> T -> Y_b -> T (-> Y_b); R_bb = R_last ... R_1.
     const bool robust = c.opt.shifted_fallback != 0;
     double* Rbb = R ? R + c0 + int64_t(c0) * L : nullptr;
+    if (!sharded && orth_tc_supported(m, w)) {
+      // all CholeskyQR passes of the block in one kernel (orth_tc.cu)
+      orth_tc(Yb, Y.ld, m, w, Rbb, L, tscratch, robust ? 1 : 0, c.status, c.h->device, c.s);
+      c0 += w;
+      continue;
+    }
     // pass 1: Y_b -> T
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w);
     if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);

@@ -72,7 +72,7 @@ __device__ __forceinline__ void fwd_subst32(float (&v)[kB], const float* L, int 
 // factor is broadcast through colbuf (two halves of 32 floats used in turn,
 // so one __syncwarp per pivot suffices) and read back as float4.  Returns
 // false in every lane when a pivot is not positive and finite.
-__device__ __noinline__ bool warp_chol32(float* A, int ld, int k0, float* dinv, float* colbuf, int lane) {
+static __device__ __noinline__ bool warp_chol32(float* A, int ld, int k0, float* dinv, float* colbuf, int lane) {
   float a[kB];
 #pragma unroll
   for (int c = 0; c < kB; ++c) a[c] = A[(k0 + lane) + (k0 + c) * ld];

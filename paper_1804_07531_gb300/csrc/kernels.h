@@ -153,6 +153,15 @@ void flip_by_peaks(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int6
 enum CholMode { CHOL_PLAIN = 0, CHOL_SHIFT_IF_NEEDED = 1, CHOL_IF_FLAGGED = 2, CHOL_SHIFT_IF_FLAGGED = 3 };
 void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int mode,
               int* needs_more, int* status, cudaStream_t s);
+// CholeskyQR2 of one column block (w <= 128 columns at Y, rows m, column-
+// major, in place) in one cooperative persistent kernel with tensor-core row
+// products (orth_tc.cu); shifted CholeskyQR3 after a breakdown, or the
+// four-pass form with robust.  R (w x w, ld ldr) receives the triangular
+// factor when not null.  scratch: orth_tc_scratch_doubles(w) doubles.
+bool orth_tc_supported(int64_t m, int w);
+size_t orth_tc_scratch_doubles(int w);
+void orth_tc(float* Y, int64_t ldy, int64_t m, int w, double* R, int ldr, double* scratch, int robust, int* status,
+             int device, cudaStream_t s);
 // *sel = the minimum-variance l_c (Section 6.6) from nl trial spectra of k
 // singular values each (lam[l_c * k + i]).
 void minvar_select(const float* lam, int nl, int k, int* sel, cudaStream_t s);
