@@ -64,7 +64,7 @@ struct TcArgs {
   int w;
   double* R;          // the block's triangular factor (w x w, ld ldr), or null
   int ldr;
-  double* G;          // FP64 Gram buffers G1..G4 (w x w each), zero at launch
+  float* G;           // Gram buffers G1..G4 (FP32, row-major 128 x 128 each, lower part), zero at launch
   unsigned* ctr;      // grid-barrier counter, zero at launch
   int* gabort;        // raised when a barrier timed out, zero at launch
   int* status;
@@ -146,7 +146,7 @@ __device__ __forceinline__ void chunk_stage(uint8_t* ch, const ChunkRegs& cr) {
 // operands: line = column (M or N index), 64 rows per line and box.
 __device__ __forceinline__ void issue_gram(uint32_t tmem, uint32_t ch, bool accumulate) {
   constexpr uint32_t kId = idesc_bf16(128, false);
-#pragma unroll
+#pragma unroll 1
   for (int s = 0; s < 8; ++s) {
     const uint32_t off = uint32_t(s >> 2) * kBox + uint32_t(s & 3) * 32u;
     const uint64_t dh = sw128_desc(ch + off, 16, 1024);
@@ -170,6 +170,7 @@ __host__ __device__ constexpr uint32_t idesc_bf16_bmn(int n) {
 // rows of one half, K = 16 columns per step = 16 lines).
 __device__ __forceinline__ void issue_apply(uint32_t tmem, uint32_t rt, uint32_t ch, int ksteps) {
   constexpr uint32_t kId = idesc_bf16_bmn(64);
+#pragma unroll 1
   for (int s = 0; s < ksteps; ++s) {
     const uint32_t aoff = uint32_t(s >> 2) * kBox + uint32_t(s & 3) * 32u;
     const uint64_t ah = sw128_desc(rt + aoff, 16, 1024);
@@ -207,32 +208,50 @@ __device__ __forceinline__ bool mma_done(Sync& s) {
   return __syncthreads_and(ok) != 0;
 }
 
-// S, X (this CTA's Gram partial) -> lower part of the FP64 buffer g:
-// G(i, j) = S_ij + X_ij + X_ji for i >= j.  Warp w reads lane quarter w % 4
-// (Gram row i) and column half w / 4.
-__device__ __forceinline__ void flush_gram(const TcArgs& a, uint32_t tmem, double* g) {
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// S, X (this CTA's Gram partial) -> the lower part of the row-major FP32
+// buffer g (ld kW): G(i, j) = S_ij + X_ij + X_ji for j <= i, four entries of a
+// row per vector reduction (entries above the diagonal in the last group
+// receive zeros and are never read).  X goes through shared memory (xs: 128 x
+// 129 floats, free once the pass's last MMA has completed) so that thread i
+// also sees column i.  The FP32 sum over the CTAs is far below the rounding
+// of the FP32 Cholesky that reads it.  Warp w reads lane quarter w % 4 (Gram
+// row i) and column half w / 4.
+__device__ __noinline__ void flush_gram(const TcArgs& a, uint32_t tmem, float* g, float* xs) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = (warp & 3) * 32 + lane, j0 = (warp >> 2) * 64;
   const uint32_t lb = tmem + (uint32_t((warp & 3) * 32) << 16);
-  for (int gq = 0; gq < 4; ++gq) {
-    float s[16], x[16];
-    tmem_ld16(lb + kColS + uint32_t(j0 + 16 * gq), s);
-    tmem_ld16(lb + kColX + uint32_t(j0 + 16 * gq), x);
-    if (i >= a.w) continue;
+  float s[64];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const int j = j0 + 16 * gq + t;
-      if (j >= a.w) continue;
-      if (j <= i) atomicAdd(g + i + int64_t(j) * a.w, double(s[t]) + double(x[t]));
-      if (j >= i) atomicAdd(g + j + int64_t(i) * a.w, double(x[t]));
-    }
+  for (int gq = 0; gq < 4; ++gq) {
+    float x[16], t[16];
+    tmem_ld16(lb + kColX + uint32_t(j0 + 16 * gq), x);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) xs[i * 129 + j0 + 16 * gq + u] = x[u];
+    tmem_ld16(lb + kColS + uint32_t(j0 + 16 * gq), t);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) s[16 * gq + u] = t[u] + x[u];
+  }
+  __syncthreads();
+  if (i >= a.w) return;
+#pragma unroll
+  for (int t = 0; t < 64; t += 4) {
+    const int j = j0 + t;
+    if (j > i) break;
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (j + u <= i) ? s[t + u] + xs[(j + u) * 129 + i] : 0.f;
+    red_add_v4(g + i * kW + j, v[0], v[1], v[2], v[3]);
   }
 }
 
 // Epilogue of an apply: Q_ch^T from TMEM (lane = output column n, columns =
 // rows) -> Y rows (FP32) and, for the next pass's Gram, the staged chunk.
 // Warp w: output columns 32 (w % 4) .. + 31, rows of half w / 4.
-__device__ __forceinline__ void apply_epilogue(const TcArgs& a, uint32_t tmem, int64_t row0, uint8_t* ch,
+__device__ __noinline__ void apply_epilogue(const TcArgs& a, uint32_t tmem, int64_t row0, uint8_t* ch,
                                                bool restage) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = (warp & 3) * 32 + lane, half = warp >> 2;
@@ -271,10 +290,10 @@ __device__ __forceinline__ void apply_epilogue(const TcArgs& a, uint32_t tmem, i
   }
 }
 
-// The Gram of one pass (FP64, w x w, lower part) -> L and R^{-1} in shared
-// memory.  Returns 0, LR_ERR_NONFINITE or LR_ERR_BREAKDOWN (the same in every
-// CTA: every CTA reads the same Gram).
-__device__ int factor(const TcArgs& a, const double* g, int N, bool shift, uint8_t* base, int* sh, double* tr) {
+// The Gram of one pass (FP32, row-major ld 128, lower part) -> L and R^{-1}
+// in shared memory.  Returns 0, LR_ERR_NONFINITE or LR_ERR_BREAKDOWN (the
+// same in every CTA: every CTA reads the same Gram).
+__device__ __noinline__ int factor(const TcArgs& a, const float* g, int N, bool shift, uint8_t* base, int* sh, double* tr) {
   float* A = reinterpret_cast<float*>(base);
   float* Xd = reinterpret_cast<float*>(base + kOffXd);
   float* Xt = reinterpret_cast<float*>(base + kOffXt);
@@ -285,26 +304,44 @@ __device__ int factor(const TcArgs& a, const double* g, int N, bool shift, uint8
   if (tid == 0) *sh = 0;
   __syncthreads();
   bool bad = false;
-  for (int base_i = tid; base_i < N * N; base_i += 8 * kThreadsT) {
-    double gv[8];
+  // four entries of row r of the lower part per load; consecutive threads
+  // take consecutive rows, so the column-major stores into A and Xt fall in
+  // distinct banks
+  for (int base_i = tid; base_i < N * (N / 4); base_i += 16 * kThreadsT) {
+    float4 gv[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base_i + u * kThreadsT, r = idx % N, c = idx / N;
-      gv[u] = (idx < N * N && r < w && c < w && r >= c) ? __ldcg(g + r + int64_t(c) * w) : (r == c ? 1.0 : 0.0);
+    for (int u = 0; u < 16; ++u) {
+      const int idx = base_i + u * kThreadsT, r = idx % N, c = 4 * (idx / N);
+      gv[u] = (idx < N * (N / 4) && r < w && c <= r) ? __ldcg(reinterpret_cast<const float4*>(g + r * kW + c))
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base_i + u * kThreadsT, r = idx % N, c = idx / N;
-      if (idx >= N * N) continue;
-      if (!isfinite(gv[u])) bad = true;
-      A[r + c * kLd] = float(gv[u]);
-      Xt[r + c * kLd] = 0.f;
+    for (int u = 0; u < 16; ++u) {
+      const int idx = base_i + u * kThreadsT, r = idx % N, c = 4 * (idx / N);
+      if (idx >= N * (N / 4)) continue;
+      const float e[4] = {gv[u].x, gv[u].y, gv[u].z, gv[u].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int cc = c + q;
+        float v = e[q];
+        if (!(r < w && cc < w && cc <= r)) v = (r == cc) ? 1.f : 0.f;  // identity padding, upper part zero
+        if (!isfinite(v)) bad = true;
+        A[r + cc * kLd] = v;
+        Xt[r + cc * kLd] = 0.f;
+      }
     }
   }
   if (bad) *sh = 1;
   if (tid < 32) {
+    float d[kW / 32];
+#pragma unroll
+    for (int q = 0; q < kW / 32; ++q) {
+      const int i = tid + 32 * q;
+      d[q] = i < w ? __ldcg(g + i * kW + i) : 0.f;
+    }
     double t = 0.0;
-    for (int i = tid; i < w; i += 32) t += __ldcg(g + i + int64_t(i) * w);
+#pragma unroll
+    for (int q = 0; q < kW / 32; ++q) t += double(d[q]);
     t = warp_sum(t);
     if (tid == 0) *tr = t;
   }
@@ -386,14 +423,14 @@ __device__ void run(const TcArgs& a, uint8_t* smem, uint32_t tmem, Sync& sy, int
       if (c + G < nchunks) chunk_load(a, (c + G) * kRows, cr);  // overlaps the MMAs
       if (!mma_done(sy)) return;
     }
-    flush_gram(a, tmem, a.G);
+    flush_gram(a, tmem, a.G, reinterpret_cast<float*>(ch));
   }
   if (!gridsync::sync(a.ctr, a.gabort, a.status, bar++, sh)) return;
 
   int npass = 2;
   bool shifted = false;
   for (int pass = 0; pass < npass; ++pass) {
-    const double* g = a.G + int64_t(pass) * w * w;
+    const float* g = a.G + pass * kW * kW;
     int err;
     if (pass == 0) {
       err = factor(a, g, N, false, smem, sh, tr);
@@ -431,11 +468,13 @@ __device__ void run(const TcArgs& a, uint8_t* smem, uint32_t tmem, Sync& sy, int
         tc_fence_after();
         issue_gram(tmem, ch_s, !first);
       }
+      // the next chunk's rows (other rows than this chunk's) load while the
+      // Gram MMAs run
       if (c + G < nchunks) chunk_load(a, (c + G) * kRows, cr);
       if (gram_next && !mma_done(sy)) return;
     }
     if (gram_next) {
-      flush_gram(a, tmem, a.G + int64_t(pass + 1) * w * w);
+      flush_gram(a, tmem, a.G + (pass + 1) * kW * kW, reinterpret_cast<float*>(ch));
       if (!gridsync::sync(a.ctr, a.gabort, a.status, bar++, sh)) return;
     }
   }
@@ -476,7 +515,7 @@ __global__ void __launch_bounds__(kThreadsT, 1) orth_tc_kernel(TcArgs a) {
 
 bool orth_tc_supported(int64_t m, int w) { return m >= 1 && w >= 1 && w <= kW; }
 
-size_t orth_tc_scratch_doubles(int w) { return 4 * size_t(w) * w + 64; }
+size_t orth_tc_scratch_doubles(int) { return 4 * size_t(kW) * kW / 2 + 64; }
 
 void orth_tc(float* Y, int64_t ldy, int64_t m, int w, double* R, int ldr, double* scratch, int robust, int* status,
              int device, cudaStream_t s) {
@@ -500,7 +539,7 @@ void orth_tc(float* Y, int64_t ldy, int64_t m, int w, double* R, int ldr, double
   a.w = w;
   a.R = R;
   a.ldr = ldr;
-  a.G = scratch;
+  a.G = reinterpret_cast<float*>(scratch);
   a.ctr = reinterpret_cast<unsigned*>(scratch + red - 64);
   a.gabort = reinterpret_cast<int*>(scratch + red - 32);
   a.status = status;
