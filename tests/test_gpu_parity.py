@@ -136,6 +136,23 @@ def test_orth_matches_householder(m, ell):
     assert np.abs(q64 - qo).max() < 1e-4
 
 
+@pytest.mark.parametrize("m,ell", [(127, 5), (129, 64), (1001, 100), (257, 128), (4099, 33), (20001, 120)])
+def test_orth_ragged_panels(m, ell):
+    """Panels whose rows are not a multiple of the 128-row chunk (and odd
+    leading dimensions, so the element-wise load path), fewer rows than one
+    chunk, and block widths that are not multiples of 32."""
+    y = S.gaussian(m, ell, seed=3 * m + ell).astype(np.float32)
+    y[:, 1:] += 0.25 * y[:, :1]
+    q, r = api().orth(t32(y))
+    assert_status_ok()
+    qo, ro = L.householder_qr(y.astype(np.float64))
+    q64, r64 = f64(q), f64(r)
+    assert np.abs(q64.T @ q64 - np.eye(ell)).max() < 1e-5
+    assert rel_f(q64 @ r64, y.astype(np.float64)) < 1e-5
+    assert rel_f(r64, ro) < 1e-5
+    assert np.abs(q64 - qo).max() < 1e-4
+
+
 # ------------------------------------------------------------ algorithms
 @pytest.fixture(scope="module")
 def c1():
