@@ -148,8 +148,8 @@ void flip_by_peaks(float* U, int64_t ldu, int64_t m, float* V, int64_t ldv, int6
 // ---------------------------------------------------- small dense kernels
 // Cholesky of an FP64-accumulated Gram (ell <= 128) in one CTA:
 //   G (ell x ell, FP64 col-major, ld ell) = R^T R; writes Rinv (FP32,
-//   ell x ell, ldr); Racc (FP64, ldacc) <- R (init_acc) or R * Racc.
-//   Racc may be nullptr.  Breakdown / non-finite -> status.
+//   ell x ell, ldr) and, unless Racc is nullptr, Racc (FP64, ldacc) = R
+//   (init_acc must be true).  Breakdown / non-finite -> status.
 enum CholMode { CHOL_PLAIN = 0, CHOL_SHIFT_IF_NEEDED = 1, CHOL_IF_FLAGGED = 2, CHOL_SHIFT_IF_FLAGGED = 3 };
 void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int ldacc, bool init_acc, int mode,
               int* needs_more, int* status, cudaStream_t s);
