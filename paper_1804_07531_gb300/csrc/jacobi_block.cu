@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
   float* vi = wn + 64;              // 1/|v| of the local columns
   __shared__ __align__(8) uint64_t full;  // the blocks of the next round landed
   __shared__ unsigned rot_total;          // rotations so far, all CTAs
+  __shared__ unsigned off_bits[2];        // largest |gamma| / sqrt(alpha beta) of a sweep (by parity), all CTAs
   __shared__ unsigned abort_total;        // CTAs that timed out
   __shared__ int timed_out;
   auto slot = [&](int buf, int s) { return sm + size_t(buf * 2 + s) * ws; };
@@ -305,6 +306,8 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     rot_total = 0;
+    off_bits[0] = 0;
+    off_bits[1] = 0;
     abort_total = 0;
     timed_out = 0;
   }
@@ -314,7 +317,16 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
 
   const float tol = 1.2e-7f * sqrtf(float(n));
   const float tol2 = tol * tol;
+  // Early stop: the cyclic sweeps converge quadratically, the largest
+  // relative off-diagonal of a sweep falling to about 10 times the square of
+  // the previous one's (FP64 emulation of this schedule on the workload's
+  // core: 8e-4, then 4e-6, then a sweep without rotations).  A sweep whose
+  // largest one is below sqrt(tol / 1e4) leaves every pair below tol for any
+  // constant up to 1e4, so the loop ends there instead of running one more
+  // sweep that would rotate nothing.
+  const float stop_off = sqrtf(tol * 1e-4f);
   const uint32_t rot_l = smem_u32(&rot_total), abort_l = smem_u32(&abort_total);
+  const uint32_t off_l = smem_u32(&off_bits[0]);  // off_bits[1] follows at + 4
   int cur = 0, rpos = 0, jb = 0;  // W buffer, block round it is placed for, J buffer
   bool pend = false;              // J of the previous block round waits for V
   int pk0 = 0, pk1 = 0;           // its blocks
@@ -324,6 +336,7 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
   int sweep = 0;
   for (; sweep < kMaxSweeps && !done; ++sweep) {
     unsigned myrot = 0;  // this lane's rotations in the sweep (group lane 0)
+    float myoff = 0.f;   // this group's largest |gamma| / sqrt(alpha beta) in the sweep
     for (int r = 0; r < NB - 1; ++r) {
       int c0, c1;
       round_pair(rank, r, NB, c0, c1);
@@ -350,6 +363,7 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
             jy.load(J, q, gl);
             float al, be, ga, c, s;
             dots<TM>(x, y, al, be, ga);
+            if (live && al > 0.f && be > 0.f) myoff = fmaxf(myoff, fabsf(ga) * rsqrtf(al * be));
             if (live && angle(al, be, ga, tol2, c, s)) {
               const float2 c2 = make_float2(c, c), s2 = make_float2(s, s), ms2 = make_float2(-s, -s);
 #pragma unroll
@@ -384,6 +398,7 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
             jy.load(J, live ? b + q : b, gl);
             float al, be, ga, c, s;
             dots<TM>(a, y, al, be, ga);
+            if (live && al > 0.f && be > 0.f) myoff = fmaxf(myoff, fabsf(ga) * rsqrtf(al * be));
             if (live && angle(al, be, ga, tol2, c, s)) {
               const float2 c2 = make_float2(c, c), s2 = make_float2(s, s), ms2 = make_float2(-s, -s);
 #pragma unroll
@@ -417,12 +432,16 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
         if (sweep_end) {
           const unsigned wr = __reduce_add_sync(0xffffffffu, myrot);
           if (lane == 0 && wr) atomicAdd(&rot_total, wr);
+          const unsigned wo = __reduce_max_sync(0xffffffffu, __float_as_uint(myoff));
+          if (lane == 0) atomicMax(&off_bits[sweep & 1], wo);
         }
         __syncthreads();
         const unsigned tot = *static_cast<volatile unsigned*>(&rot_total);
-        done = tot == seen;
+        const float offmax = __uint_as_float(*static_cast<volatile unsigned*>(&off_bits[sweep & 1]));
+        done = tot == seen || offmax < stop_off;
         seen = tot;
         __syncthreads();
+        if (tid == 0) off_bits[(sweep + 1) & 1] = 0;
         continue;
       }
 
@@ -435,6 +454,9 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
       if (sweep_end) {
         const unsigned wr = __reduce_add_sync(0xffffffffu, myrot);
         if (wr && lane < P) asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(mapa(rot_l, lane)), "r"(wr) : "memory");
+        const unsigned wo = __reduce_max_sync(0xffffffffu, __float_as_uint(myoff));
+        if (wo && lane < P)
+          asm volatile("red.shared::cluster.max.u32 [%0], %1;" ::"r"(mapa(off_l + 4u * uint32_t(sweep & 1), lane)), "r"(wo) : "memory");
       }
       if (local_abort && tid < P)
         asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(mapa(abort_l, tid)), "r"(1u) : "memory");
@@ -459,6 +481,8 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
       // barrier, and this one arrives only after these reads)
       const unsigned ab = *static_cast<volatile unsigned*>(&abort_total);
       const unsigned tot = sweep_end ? *static_cast<volatile unsigned*>(&rot_total) : 0u;
+      const float offmax =
+          sweep_end ? __uint_as_float(*static_cast<volatile unsigned*>(&off_bits[sweep & 1])) : 0.f;
       if (ab) {
         done = true;  // some CTA gave up: all leave here, nothing moves
         break;
@@ -487,8 +511,11 @@ __global__ void __launch_bounds__(TM == 16 ? kThreadsTM16 : kMaxThreads, 1)
       cur ^= 1;
       rpos = rn;
       if (sweep_end) {
-        done = tot == seen;  // no rotation anywhere in this sweep
+        // no rotation anywhere in this sweep, or (early stop) none left to
+        // reach tol in the next one
+        done = tot == seen || offmax < stop_off;
         seen = tot;
+        if (tid == 0) off_bits[(sweep + 1) & 1] = 0;  // no CTA adds to it before the next sweep's last exchange
       }
     }
   }
