@@ -830,7 +830,10 @@ void run_pinched(Ctx& c, const lr_operator* J, int k, int ell, int v, const Mat&
 }
 
 // ------------------------------------------------------------ Alg. 9
-void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o) {
+// first_range, when given, computes the first view Y = A Omega in place of
+// view_range (the host-buffer entry point overlaps it with A's copy).
+void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Outs& o,
+                const std::function<void(Ctx&, const Mat&, Mat)>* first_range = nullptr) {
   ArenaScope sc(c.ar);
   const bool even = v % 2 == 0;
   const int nb = even ? v / 2 : (v - 1) / 2;
@@ -849,7 +852,8 @@ void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Out
     const bool odd = j % 2 == 1;
     const bool in_k = odd == even;
     Mat out = in_k ? Mat{K.col(int64_t(blk) * ell), kdim, ell, kdim} : Tb;
-    if (odd) view_range(c, A, prev, out);
+    if (j == 1 && first_range) (*first_range)(c, prev, out);
+    else if (odd) view_range(c, A, prev, out);
     else view_corange(c, A, prev, out);
     if (j < v - 1) orth(c, out, nullptr);
     if (in_k) ++blk;
@@ -1839,12 +1843,42 @@ lr_status lr_block_krylov_host(lr_handle h, const lr_mat* A_host, int k, int p, 
     o.U = Mat{c.ar.take<float>(size_t(a.m) * k), a.m, k, a.m};
     o.V = Mat{c.ar.take<float>(size_t(a.n) * k), a.n, k, a.n};
     o.S = c.ar.take<float>(size_t(k));
-    LR_CHECK_CUDA(cudaMemcpyAsync(a_dev, A_host->data, size_t(a.m) * size_t(a.ld) * a.elem(), cudaMemcpyHostToDevice,
-                                  c.s));
     LR_CHECK_CUDA(cudaMemcpy2DAsync(om.p, size_t(om.ld) * 4, om_h.p, size_t(om_h.ld) * 4, size_t(a.n) * 4, size_t(ell),
                                     cudaMemcpyHostToDevice, c.s));
     a.p = a_dev;
-    run_krylov(c, a, k, ell, v, om, o);
+    // A crosses the host link in row blocks on the handle's copy stream; the
+    // first view (Y = A Omega, rows r0 .. of Y from rows r0 .. of A) runs on
+    // each block as soon as it has landed, so it hides under the copy of the
+    // later blocks; the other views start once all of A is on the device.
+    const std::function<void(Ctx&, const Mat&, Mat)> first = [&](Ctx& cc, const Mat& X, Mat Y) {
+      ArenaScope fs(cc.ar);
+      SplitOp pre = convert_operand(cc, a, X.p, X.ld, a.n, int(X.cols));
+      if (cc.measure) return;
+      lr_handle hh = cc.h;
+      if (!hh->copy_stream) {
+        LR_CHECK_CUDA(cudaStreamCreateWithFlags(&hh->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+          LR_CHECK_CUDA(cudaEventCreateWithFlags(&hh->copied[i], cudaEventDisableTiming));
+          LR_CHECK_CUDA(cudaEventCreateWithFlags(&hh->consumed[i], cudaEventDisableTiming));
+        }
+      }
+      zero_f32(Y.p, Y.rows, Y.cols, Y.ld, cc.s);
+      // the copies start after everything already queued on the caller's stream
+      LR_CHECK_CUDA(cudaEventRecord(hh->consumed[0], cc.s));
+      LR_CHECK_CUDA(cudaStreamWaitEvent(hh->copy_stream, hh->consumed[0], 0));
+      const int64_t rb = std::max<int64_t>(256, (a.m / 8 + 255) / 256 * 256);
+      const size_t row_bytes = size_t(a.ld) * a.elem();
+      for (int64_t r0 = 0, b = 0; r0 < a.m; r0 += rb, ++b) {
+        const int64_t rows = std::min(rb, a.m - r0);
+        LR_CHECK_CUDA(cudaMemcpyAsync(a_dev + size_t(r0) * row_bytes,
+                                      static_cast<const char*>(A_host->data) + size_t(r0) * row_bytes,
+                                      size_t(rows) * row_bytes, cudaMemcpyHostToDevice, hh->copy_stream));
+        LR_CHECK_CUDA(cudaEventRecord(hh->copied[b & 1], hh->copy_stream));
+        LR_CHECK_CUDA(cudaStreamWaitEvent(cc.s, hh->copied[b & 1], 0));
+        view_band(cc, a, 0, X.p, X.ld, int(X.cols), Y.p, Y.ld, r0, rows, &pre);
+      }
+    };
+    run_krylov(c, a, k, ell, v, om, o, &first);
     LR_CHECK_CUDA(cudaMemcpy2DAsync(oh.U.p, size_t(oh.U.ld) * 4, o.U.p, size_t(o.U.ld) * 4, size_t(a.m) * 4, size_t(k),
                                     cudaMemcpyDeviceToHost, c.s));
     LR_CHECK_CUDA(cudaMemcpy2DAsync(oh.V.p, size_t(oh.V.ld) * 4, o.V.p, size_t(o.V.ld) * 4, size_t(a.n) * 4, size_t(k),
