@@ -47,10 +47,13 @@ std::atomic<uint64_t> g_kernel_launches{0};
 namespace lr {
 namespace {
 
-// FP32 column-major thin matrix.
+// FP32 column-major thin matrix; bf (when not null) a BF16 copy of it that a
+// thin QR leaves for the BF16 views (column-major, ld ldbf).
 struct Mat {
   float* p = nullptr;
   int64_t rows = 0, cols = 0, ld = 0;
+  __nv_bfloat16* bf = nullptr;
+  int64_t ldbf = 0;
   float* col(int64_t c) const { return p + c * ld; }
 };
 
@@ -427,13 +430,15 @@ void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
 // QR, as the first block of a Krylov basis is); they are kept as they are
 // and only the remaining columns are projected and factorised (R must then
 // be null).
-void orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
+// Returns true when Y.bf is set and every factorised block left its BF16
+// copy there (the single-kernel thin QR does; the other paths do not).
+bool orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
   const int64_t m = Y.rows;
   // sharded: Y holds this rank's rows; the caller checks the total
   LR_REQUIRE(sharded || m >= Y.cols, LR_ERR_SHAPE, "orth needs rows >= cols");
   LR_REQUIRE(done == 0 || R == nullptr, LR_ERR_INVALID_ARG, "orth: R is not formed for kept columns");
   const int L = int(Y.cols) - done;
-  if (L <= 0) return;
+  if (L <= 0) return Y.bf != nullptr;
   ArenaScope sc(c.ar);
   const int nb = (L + kMaxBlock - 1) / kMaxBlock;
   const int wmax = (L + nb - 1) / nb;
@@ -444,7 +449,8 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
   double* R2 = c.ar.take<double>(size_t(wmax) * wmax);  // factor of a later pass
   int* flags = c.ar.take<int>(size_t(nb));
   double* tscratch = c.ar.take<double>(orth_tc_scratch_doubles(wmax));
-  if (c.measure) return;
+  if (c.measure) return false;
+  bool all_bf = Y.bf != nullptr;
   TraceScope tr(c, LR_TRACE_ORTH);
   if (R) LR_CHECK_CUDA(cudaMemsetAsync(R, 0, size_t(L) * L * sizeof(double), c.s));
   LR_CHECK_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * nb, c.s));
@@ -477,10 +483,12 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
     double* Rbb = R ? R + c0 + int64_t(c0) * L : nullptr;
     if (!sharded && orth_tc_supported(m, w)) {
       // all CholeskyQR passes of the block in one kernel (orth_tc.cu)
-      orth_tc(Yb, Y.ld, m, w, Rbb, L, tscratch, robust ? 1 : 0, c.status, c.h->device, c.s);
+      orth_tc(Yb, Y.ld, m, w, Rbb, L, tscratch, robust ? 1 : 0, c.status, c.h->device, c.s,
+              Y.bf ? Y.bf + int64_t(c0) * Y.ldbf : nullptr, Y.ldbf);
       c0 += w;
       continue;
     }
+    all_bf = false;  // this block takes the separate kernels
     // pass 1: Y_b -> T
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w);
     if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
@@ -511,6 +519,7 @@ void orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
     }
     c0 += w;
   }
+  return all_bf;
 }
 
 // ------------------------------------------------ triangular inverse
@@ -846,29 +855,55 @@ void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Out
   float* W = c.ar.take<float>(size_t(Lk) * Lk);
   float* Vj = c.ar.take<float>(size_t(Lk) * Lk);
   float* Sv = c.ar.take<float>(size_t(Lk));
+  if (A.bf16) {
+    // the thin QRs leave the BF16 copies the next BF16 views read
+    K.ldbf = round8(kdim);
+    K.bf = c.ar.take<__nv_bfloat16>(size_t(K.ldbf) * Lk);
+    Tb.ldbf = round8(odim);
+    Tb.bf = c.ar.take<__nv_bfloat16>(size_t(Tb.ldbf) * ell);
+  }
+  // a view of A with X: from X's BF16 copy when one is valid
+  auto view = [&](const Mat& X, Mat Y, int mode, bool valid_bf, bool last) {
+    if (!(A.bf16 && valid_bf && X.bf) || (last && c.opt.split_last)) {
+      if (mode == 0) view_range(c, A, X, Y, last);
+      else view_corange(c, A, X, Y, last);
+      return;
+    }
+    if (!c.measure) zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
+    SplitOp pre;
+    pre.bf = X.bf;
+    pre.ld = X.ldbf;
+    view_band(c, A, mode, X.p, X.ld, int(X.cols), Y.p, Y.ld, 0, A.m, &pre);
+  };
   Mat prev = Om;
+  bool prev_bf = false;
+  bool k0_bf = false;  // K's first block has its BF16 copy
   int blk = 0;
   for (int j = 1; j <= v - 1; ++j) {
     const bool odd = j % 2 == 1;
     const bool in_k = odd == even;
-    Mat out = in_k ? Mat{K.col(int64_t(blk) * ell), kdim, ell, kdim} : Tb;
+    Mat out = in_k ? Mat{K.col(int64_t(blk) * ell), kdim, ell, kdim,
+                         K.bf ? K.bf + int64_t(blk) * ell * K.ldbf : nullptr, K.ldbf}
+                   : Tb;
     if (j == 1 && first_range) (*first_range)(c, prev, out);
-    else if (odd) view_range(c, A, prev, out);
-    else view_corange(c, A, prev, out);
-    if (j < v - 1) orth(c, out, nullptr);
+    else view(prev, out, odd ? 0 : 1, prev_bf, false);
+    prev_bf = false;
+    if (j < v - 1) prev_bf = orth(c, out, nullptr);
+    if (in_k && blk == 0) k0_bf = prev_bf;
     if (in_k) ++blk;
     prev = out;
   }
   // Q = qr(K); K's first block is already orthonormal (the qr of an inner
   // view) unless it is the raw last block itself
-  orth(c, K, nullptr, nb >= 2 ? ell : 0);
+  const bool rest_bf = orth(c, K, nullptr, nb >= 2 ? ell : 0);
+  const bool K_bf = rest_bf && (nb < 2 || k0_bf);
   if (even) {
-    view_corange(c, A, K, F, true);      // A^T Q_c
+    view(K, F, 1, K_bf, true);           // A^T Q_c
     orth(c, F, Rf);                      // [Q_r, R_r]
     core_svd(c, Rf, Lk, W, Vj, Sv);      // R_r = V^ L U^T
     write_outputs(c, K, Vj, F, W, Lk, Sv, k, o);
   } else {
-    view_range(c, A, K, F, true);        // A Q_r
+    view(K, F, 0, K_bf, true);           // A Q_r
     orth(c, F, Rf);                      // [Q_c, R_c]
     core_svd(c, Rf, Lk, W, Vj, Sv);      // R_c = U^ L V^T
     write_outputs(c, F, W, K, Vj, Lk, Sv, k, o);

@@ -158,10 +158,11 @@ void chol_inv(const double* G, int ell, float* Rinv, int ldr, double* Racc, int 
 // products (orth_tc.cu); shifted CholeskyQR3 after a breakdown, or the
 // four-pass form with robust.  R (w x w, ld ldr) receives the triangular
 // factor when not null.  scratch: orth_tc_scratch_doubles(w) doubles.
+// ybf (optional): a BF16 copy of the final Q (column-major, ld ldbf).
 bool orth_tc_supported(int64_t m, int w);
 size_t orth_tc_scratch_doubles(int w);
 void orth_tc(float* Y, int64_t ldy, int64_t m, int w, double* R, int ldr, double* scratch, int robust, int* status,
-             int device, cudaStream_t s);
+             int device, cudaStream_t s, __nv_bfloat16* ybf = nullptr, int64_t ldbf = 0);
 // *sel = the minimum-variance l_c (Section 6.6) from nl trial spectra of k
 // singular values each (lam[l_c * k + i]).
 void minvar_select(const float* lam, int nl, int k, int* sel, cudaStream_t s);

@@ -70,6 +70,8 @@ struct TcArgs {
   int* status;
   int robust;
   int vec;            // Y allows float4 access (16-byte aligned, ld % 4 == 0)
+  __nv_bfloat16* ybf; // when not null: BF16 copy of the final Q (ld ldbf, a multiple of 8, 16-byte aligned)
+  int64_t ldbf;
 };
 
 // x = h + m + l in BF16, each term the rounding of the remainder.
@@ -274,6 +276,24 @@ __device__ __noinline__ void apply_epilogue(const TcArgs& a, uint32_t tmem, int6
     } else {
       for (int j = 0; j < 64; ++j)
         if (r0 + j < a.m) p[j] = v[j];
+    }
+  }
+  if (!restage && a.ybf && n < a.w && r0 < a.m) {
+    // the last pass also leaves the BF16 copy that a BF16 view of Q reads
+    __nv_bfloat16* q = a.ybf + r0 + int64_t(n) * a.ldbf;
+    if (r0 + 64 <= a.m) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          w4[t] = uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(v[8 * u + 2 * t]))) |
+                  (uint32_t(__bfloat16_as_ushort(__float2bfloat16_rn(v[8 * u + 2 * t + 1]))) << 16);
+        *reinterpret_cast<uint4*>(q + 8 * u) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+      }
+    } else {
+      for (int j = 0; j < 64; ++j)
+        if (r0 + j < a.m) q[j] = __float2bfloat16_rn(v[j]);
     }
   }
   if (restage) {
@@ -518,7 +538,7 @@ bool orth_tc_supported(int64_t m, int w) { return m >= 1 && w >= 1 && w <= kW; }
 size_t orth_tc_scratch_doubles(int) { return 4 * size_t(kW) * kW / 2 + 64; }
 
 void orth_tc(float* Y, int64_t ldy, int64_t m, int w, double* R, int ldr, double* scratch, int robust, int* status,
-             int device, cudaStream_t s) {
+             int device, cudaStream_t s, __nv_bfloat16* ybf, int64_t ldbf) {
   LR_REQUIRE(orth_tc_supported(m, w), LR_ERR_UNSUPPORTED, "orth_tc: block wider than 128");
   static std::atomic<int> grid_cap[64];  // co-resident CTAs, per device
   int cap = grid_cap[device & 63].load();
@@ -545,6 +565,10 @@ void orth_tc(float* Y, int64_t ldy, int64_t m, int w, double* R, int ldr, double
   a.status = status;
   a.robust = robust;
   a.vec = (reinterpret_cast<uintptr_t>(Y) & 15) == 0 && ldy % 4 == 0;
+  LR_REQUIRE(!ybf || ((reinterpret_cast<uintptr_t>(ybf) & 15) == 0 && ldbf % 8 == 0 && ldbf >= m), LR_ERR_ALIGNMENT,
+             "orth_tc: BF16 copy not 16-byte aligned or its ld not a multiple of 8");
+  a.ybf = ybf;
+  a.ldbf = ldbf;
   const int64_t nchunks = (m + kRows - 1) / kRows;
   const int grid = int(std::min<int64_t>(cap, nchunks));
   void* args[] = {&a};
