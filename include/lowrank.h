@@ -84,9 +84,12 @@ typedef struct {
   int32_t shifted_fallback; /* 0: every thin QR retries a Cholesky breakdown of its first
                                pass with a shifted Gram and adds a third pass (shifted
                                CholeskyQR3): full-rank sketches up to kappa ~ 1e7.  1: also
-                               rank-deficient sketches (A of rank below k + p): a flagged
-                               block takes shifted, shifted, plain, plain passes; without
-                               it such a sketch ends in LR_ERR_BREAKDOWN */
+                               rank-deficient sketches (A of rank below k + p; a block
+                               Krylov basis of three or more blocks whose later blocks,
+                               projected out of the earlier ones, keep directions near FP32
+                               rounding): a flagged block takes shifted, shifted, plain,
+                               plain passes; without it such a sketch ends in
+                               LR_ERR_BREAKDOWN */
   int32_t band_mb;          /* one-read sketches (dual, chained): 0 = default: the dual
                                sketch of a BF16 A with ell1 <= 128 and ell2 <= 64 runs the
                                fused kernel that feeds each staged tile of A to both

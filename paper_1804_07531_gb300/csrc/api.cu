@@ -425,18 +425,21 @@ void view_chained(Ctx& c, const AMat& A, const Mat& X, Mat Y, Mat Z) {
 // CholeskyQR2 (Gram in FP32 products with FP64 accumulation, Cholesky and
 // triangular inverse in one CTA).  R (L x L FP64, ld L) receives the
 // triangular factor when non-null: off-diagonal blocks are the summed
-// projection coefficients, diagonal blocks R2 R1.
+// projection coefficients, diagonal blocks R2 R1; ldr is its leading
+// dimension (0: L).
 // done: leading columns already orthonormal (the output of an earlier thin
 // QR, as the first block of a Krylov basis is); they are kept as they are
-// and only the remaining columns are projected and factorised (R must then
-// be null).
+// and only the remaining columns are projected and factorised.  R's columns
+// before done are then the caller's (the earlier thin QR's factor) and are
+// left as they are.
 // Returns true when Y.bf is set and every factorised block left its BF16
 // copy there (the single-kernel thin QR does; the other paths do not).
-bool orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
+bool orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false, int ldr = 0) {
   const int64_t m = Y.rows;
   // sharded: Y holds this rank's rows; the caller checks the total
   LR_REQUIRE(sharded || m >= Y.cols, LR_ERR_SHAPE, "orth needs rows >= cols");
-  LR_REQUIRE(done == 0 || R == nullptr, LR_ERR_INVALID_ARG, "orth: R is not formed for kept columns");
+  if (ldr == 0) ldr = int(Y.cols);
+  LR_REQUIRE(ldr >= Y.cols, LR_ERR_INVALID_ARG, "orth: ldr < columns");
   const int L = int(Y.cols) - done;
   if (L <= 0) return Y.bf != nullptr;
   ArenaScope sc(c.ar);
@@ -452,7 +455,7 @@ bool orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
   if (c.measure) return false;
   bool all_bf = Y.bf != nullptr;
   TraceScope tr(c, LR_TRACE_ORTH);
-  if (R) LR_CHECK_CUDA(cudaMemsetAsync(R, 0, size_t(L) * L * sizeof(double), c.s));
+  if (R) LR_CHECK_CUDA(cudaMemsetAsync(R + int64_t(done) * ldr, 0, size_t(L) * ldr * sizeof(double), c.s));
   LR_CHECK_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * nb, c.s));
   int c0 = done;
   for (int b = 0; b < nb; ++b) {
@@ -465,7 +468,7 @@ bool orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
         if (sharded) allreduce(c, G64, int64_t(c0) * w, LR_F64);    // rows split over the ranks
         f64_to_f32(G64, c0, C32, c0, c0, w, c.s);
         gemm(c, m, w, c0, false, Y.p, Y.ld, false, C32, c0, Yb, Y.ld, -1.f, 1.f);  // Y_b -= Q_prev C
-        if (R) add_block_f64(R, L, 0, c0, G64, c0, c0, w, c.s);
+        if (R) add_block_f64(R, ldr, 0, c0, G64, c0, c0, w, c.s);
       }
     }
     // CholeskyQR2 with a breakdown-triggered shift (shifted CholeskyQR3,
@@ -480,10 +483,10 @@ bool orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
     // exactly through shifted passes, so R stays the triangular factor.
     // Passes alternate Y_b -> T -> Y_b -> T (-> Y_b); R_bb = R_last ... R_1.
     const bool robust = c.opt.shifted_fallback != 0;
-    double* Rbb = R ? R + c0 + int64_t(c0) * L : nullptr;
+    double* Rbb = R ? R + c0 + int64_t(c0) * ldr : nullptr;
     if (!sharded && orth_tc_supported(m, w)) {
       // all CholeskyQR passes of the block in one kernel (orth_tc.cu)
-      orth_tc(Yb, Y.ld, m, w, Rbb, L, tscratch, robust ? 1 : 0, c.status, c.h->device, c.s,
+      orth_tc(Yb, Y.ld, m, w, Rbb, ldr, tscratch, robust ? 1 : 0, c.status, c.h->device, c.s,
               Y.bf ? Y.bf + int64_t(c0) * Y.ldbf : nullptr, Y.ldbf);
       c0 += w;
       continue;
@@ -492,27 +495,27 @@ bool orth(Ctx& c, Mat Y, double* R, int done = 0, bool sharded = false) {
     // pass 1: Y_b -> T
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w);
     if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
-    chol_inv(G64, w, Rinv, w, Rbb, L, true, CHOL_SHIFT_IF_NEEDED, more, c.status, c.s);
+    chol_inv(G64, w, Rinv, w, Rbb, ldr, true, CHOL_SHIFT_IF_NEEDED, more, c.status, c.s);
     gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m);
     // pass 2: T -> Y_b (R_bb <- R_2 R_bb by a separate many-CTA product)
     gram64(c, w, w, m, T, m, T, m, G64, w);
     if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
     chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, robust ? CHOL_SHIFT_IF_FLAGGED : CHOL_PLAIN, more,
              c.status, c.s);
-    if (Rbb) upper_product(R2, w, Rbb, L, w, nullptr, c.s);
+    if (Rbb) upper_product(R2, w, Rbb, ldr, w, nullptr, c.s);
     gemm(c, m, w, w, false, T, m, false, Rinv, w, Yb, Y.ld);
     // pass 3 (only after a shifted pass 1): Y_b -> T -> Y_b
     gram64(c, w, w, m, Yb, Y.ld, Yb, Y.ld, G64, w, more);
     if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
     chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_IF_FLAGGED, more, c.status, c.s);
-    if (Rbb) upper_product(R2, w, Rbb, L, w, more, c.s);
+    if (Rbb) upper_product(R2, w, Rbb, ldr, w, more, c.s);
     gemm(c, m, w, w, false, Yb, Y.ld, false, Rinv, w, T, m, 1.f, 0.f, more);
     if (robust) {
       // pass 4: T -> Y_b
       gram64(c, w, w, m, T, m, T, m, G64, w, more);
       if (sharded) allreduce(c, G64, int64_t(w) * w, LR_F64);
       chol_inv(G64, w, Rinv, w, Rbb ? R2 : nullptr, w, true, CHOL_IF_FLAGGED, more, c.status, c.s);
-      if (Rbb) upper_product(R2, w, Rbb, L, w, more, c.s);
+      if (Rbb) upper_product(R2, w, Rbb, ldr, w, more, c.s);
       gemm(c, m, w, w, false, T, m, false, Rinv, w, Yb, Y.ld, 1.f, 0.f, more);
     } else {
       copy_f32(T, m, Yb, Y.ld, m, w, c.s, more);
@@ -875,6 +878,20 @@ void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Out
     pre.ld = X.ldbf;
     view_band(c, A, mode, X.p, X.ld, int(X.cols), Y.p, Y.ld, 0, A.m, &pre);
   };
+  // The final view multiplies A (or A^T) by the orthonormal basis of K,
+  // whose first block is the first inner thin-QR output, kept as it is (the
+  // later blocks are projected against it).  Its product with A^T (A) is
+  // the next inner view's output, so that view writes F's first block, whose
+  // thin QR (with its R factor) then serves both as that inner step's and
+  // as the first block of F's; the final view runs over K's other blocks.
+  // Not with split_last, whose final view is the more accurate two-term one
+  // over all of K.
+  const bool reuse = !c.opt.split_last && nb >= 2;
+  Mat F0{F.p, odim, ell, odim};  // F's first block
+  if (A.bf16 && reuse) {
+    F0.ldbf = round8(odim);
+    F0.bf = c.ar.take<__nv_bfloat16>(size_t(F0.ldbf) * ell);
+  }
   Mat prev = Om;
   bool prev_bf = false;
   bool k0_bf = false;  // K's first block has its BF16 copy
@@ -882,13 +899,14 @@ void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Out
   for (int j = 1; j <= v - 1; ++j) {
     const bool odd = j % 2 == 1;
     const bool in_k = odd == even;
+    const bool f_blk = reuse && !in_k && blk == 1;  // A^T (A) times K's first block
     Mat out = in_k ? Mat{K.col(int64_t(blk) * ell), kdim, ell, kdim,
                          K.bf ? K.bf + int64_t(blk) * ell * K.ldbf : nullptr, K.ldbf}
-                   : Tb;
+                   : f_blk ? F0 : Tb;
     if (j == 1 && first_range) (*first_range)(c, prev, out);
     else view(prev, out, odd ? 0 : 1, prev_bf, false);
     prev_bf = false;
-    if (j < v - 1) prev_bf = orth(c, out, nullptr);
+    if (j < v - 1) prev_bf = orth(c, out, f_blk ? Rf : nullptr, 0, false, Lk);
     if (in_k && blk == 0) k0_bf = prev_bf;
     if (in_k) ++blk;
     prev = out;
@@ -897,14 +915,19 @@ void run_krylov(Ctx& c, const AMat& A, int k, int ell, int v, const Mat& Om, Out
   // view) unless it is the raw last block itself
   const bool rest_bf = orth(c, K, nullptr, nb >= 2 ? ell : 0);
   const bool K_bf = rest_bf && (nb < 2 || k0_bf);
+  // the final view: all of K, or all but its first block
+  const int f0 = reuse ? ell : 0;
+  const Mat Kf{K.col(f0), kdim, Lk - f0, kdim, K.bf ? K.bf + int64_t(f0) * K.ldbf : nullptr, K.ldbf};
+  const Mat Ff{F.col(f0), odim, Lk - f0, odim};
+  const bool Kf_bf = reuse ? rest_bf : K_bf;
   if (even) {
-    view(K, F, 1, K_bf, true);           // A^T Q_c
-    orth(c, F, Rf);                      // [Q_r, R_r]
+    view(Kf, Ff, 1, Kf_bf, true);        // A^T Q_c
+    orth(c, F, Rf, f0);                  // [Q_r, R_r]
     core_svd(c, Rf, Lk, W, Vj, Sv);      // R_r = V^ L U^T
     write_outputs(c, K, Vj, F, W, Lk, Sv, k, o);
   } else {
-    view(K, F, 0, K_bf, true);           // A Q_r
-    orth(c, F, Rf);                      // [Q_c, R_c]
+    view(Kf, Ff, 0, Kf_bf, true);        // A Q_r
+    orth(c, F, Rf, f0);                  // [Q_c, R_c]
     core_svd(c, Rf, Lk, W, Vj, Sv);      // R_c = U^ L V^T
     write_outputs(c, F, W, K, Vj, Lk, Sv, k, o);
   }

@@ -175,12 +175,16 @@ def test_subspace_iteration_parity(c1, v):
     print(check_tsvd(a64, u, s, vv, uo, so, vo))
 
 
-@pytest.mark.parametrize("v", [2, 3, 4, 5])
+@pytest.mark.parametrize("v", [2, 3, 4, 5, 6, 7])
 def test_block_krylov_parity(c1, v):
+    """Two and three Krylov blocks, even and odd view counts.  At v = 7 the
+    last block of this slowly decaying spectrum (sigma_j = 1/j) keeps, once
+    projected out of the first two, directions near FP32 rounding, where the
+    plain CholeskyQR breaks down: that case takes the rank-deficient form."""
     cfg, a32, om = c1
     k, p = cfg["k"], cfg["p"]
     a64 = a32.astype(np.float64)
-    u, s, vv = api().block_krylov(t32(a32), k, p, v, t32(om))
+    u, s, vv = api().block_krylov(t32(a32), k, p, v, t32(om), shifted_fallback=v >= 7)
     assert_status_ok()
     uo, so, vo = Al.block_krylov(a64, om.astype(np.float64), k, v)
     print(check_tsvd(a64, u, s, vv, uo, so, vo))
@@ -222,16 +226,20 @@ def test_single_pass_parity(l_c):
     print(check_tsvd(a64, u, s, vv, uo, so, vo))
 
 
-@pytest.mark.parametrize("algo", ["subspace", "krylov"])
-def test_bf16_form_matches_oracle_on_bf16_matrix(algo):
-    """BF16 form: A stored in BF16 is the matrix; operands rounded to BF16."""
-    m, n, k, p, v = 4096, 2048, 20, 10, 4
+@pytest.mark.parametrize("algo,v", [("subspace", 4), ("krylov", 4), ("krylov", 5),
+                                    ("krylov", 6), ("krylov", 7)])
+def test_bf16_form_matches_oracle_on_bf16_matrix(algo, v):
+    """BF16 form: A stored in BF16 is the matrix; operands rounded to BF16.
+    Krylov with two and three blocks, even and odd view counts; three blocks
+    take the rank-deficient form of the thin QR (the third block, projected
+    out of the first two, keeps directions near FP32 rounding)."""
+    m, n, k, p = 4096, 2048, 20, 10
     a64 = S.usv(m, n, S.sigma_config("pow15", n), 31, 32)
     ab = torch.tensor(a64, dtype=torch.float32).bfloat16()
     a_exact = ab.double().numpy()
     om = S.gaussian(n, k + p, seed=33).astype(np.float32)
     fn = api().subspace_iter if algo == "subspace" else api().block_krylov
-    u, s, vv = fn(ab.to(DEV), k, p, v, t32(om))
+    u, s, vv = fn(ab.to(DEV), k, p, v, t32(om), shifted_fallback=v >= 6)
     assert_status_ok()
     ref = Al.gen_subspace_iteration if algo == "subspace" else Al.block_krylov
     uo, so, vo = ref(a_exact, om.astype(np.float64), k, v)
