@@ -14,7 +14,12 @@
 //   * the Z^T partial of each k-block (double-buffered in TMEM) is added into
 //     Z by the epilogue warps with vector reductions (red.global.add.v4.f32);
 //     Z (n x ell2 FP32) is small enough to stay in L2, so the partials are
-//     reduced there and A is the only operand streamed from HBM.
+//     reduced there and A is the only operand streamed from HBM.  For
+//     ell2 <= 64 the partial first goes through shared memory (double-
+//     buffered, one barrier of the epilogue warps per k-block), so that each
+//     warp's reduction instruction covers 512 contiguous bytes of Z (two of
+//     its columns) instead of 16 bytes in each of 32 columns: eight times
+//     fewer L2 requests, and every epilogue warp takes a share.
 // Warp roles: 0 TMA producer, 1 MMA issuer (single thread), 2-9 epilogue
 // (two warps per TMEM lane quarter).
 // Every mbarrier wait is bounded (about 2 s): on expiry the kernel records
@@ -45,19 +50,40 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
-template <int NCY, int NH>
+// Barrier of the eight epilogue warps (threads 64..319, barrier 1) that also
+// returns whether every one of them passed ok: the warps leave their loop
+// together, so none is left at a later barrier that the others never reach.
+__device__ __forceinline__ bool epi_all(bool ok) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "barrier.red.and.pred p, 1, 256, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(r)
+      : "r"(ok ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+
+constexpr int kZsRows = 64;  // staged Z^T partial: 64 columns of Z (ell2 <= 64)
+constexpr int kZsLd = 68;    // floats per staged row (64 + 4: 16-byte aligned, no bank conflicts)
+
+template <int NCY, int NH, bool ZS>
 struct DCfg {
   static constexpr uint32_t kXBytes = NCY * 128u;              // NCY rows x 64 BF16
   static constexpr uint32_t kStage = kATile + kXBytes;          // multiple of 1024
   static constexpr uint32_t kPsiBytes = 4u * NH * kPsiHalf;     // 4 K chunks of 64 strip rows
+  static constexpr uint32_t kZsBytes = ZS ? 2u * kZsRows * kZsLd * 4u : 0u;  // two staging buffers
   static constexpr int kStages =
-      int(std::min<size_t>(4, (kSmemMaxD - kPsiBytes - 2048) / kStage));
-  static constexpr size_t kSmem = size_t(kPsiBytes) + size_t(kStages) * kStage + 1024 + 256;
+      int(std::min<size_t>(4, (kSmemMaxD - kPsiBytes - kZsBytes - 2048) / kStage));
+  static constexpr size_t kSmem = size_t(kPsiBytes) + size_t(kStages) * kStage + kZsBytes + 1024 + 256;
   static constexpr uint32_t kZCol = 2 * NCY;                    // TMEM column of Z^T buffer 0
   static constexpr uint32_t kZBuf = NH * 64;                    // TMEM columns per Z^T buffer
   static_assert(kStages >= 2, "at least a double-buffered ring");
   static_assert(kZCol + 2 * kZBuf <= 512, "TMEM holds 512 FP32 columns");
   static_assert(kSmem <= kSmemMaxD, "shared memory");
+  static_assert(!ZS || NH == 1, "the staged partial is one M = 128 half");
 };
 
 struct DualParams {
@@ -73,17 +99,18 @@ struct DualParams {
   int* status;
 };
 
-template <int NCY, int NH>
+template <int NCY, int NH, bool ZS>
 __global__ void __launch_bounds__(kThreadsD, 1)
     dual_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                      const __grid_constant__ CUtensorMap tmP, DualParams p) {
-  using C = DCfg<NCY, NH>;
+  using C = DCfg<NCY, NH, ZS>;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* psi = smem;                                    // [4 chunks][NH halves] 128 x 64 BF16
   uint8_t* ring = smem + C::kPsiBytes;                    // S stages of [A tile | X tile]
-  uint64_t* full = reinterpret_cast<uint64_t*>(ring + S * C::kStage);
+  float* zst = reinterpret_cast<float*>(ring + S * C::kStage);  // [2][kZsRows][kZsLd] (ZS)
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + S * C::kStage + C::kZsBytes);
   uint64_t* empty = full + S;
   uint64_t* psi_full = empty + S;
   uint64_t* psi_empty = psi_full + 1;
@@ -262,6 +289,61 @@ __global__ void __launch_bounds__(kThreadsD, 1)
     while (ok && it < it_end) {
       const int strip = int(it / kb_n);
       const int64_t seg_end = std::min<int64_t>(it_end, int64_t(strip + 1) * kb_n);
+      if constexpr (ZS) {
+        // staged: this warp's 32 x 32 piece of the partial (Z columns
+        // q*32 + lane, k-block columns zc0 ..) -> shared memory; after the
+        // barrier, epilogue thread e reduces columns 4 (e % 16) .. + 3 of
+        // rows e / 16 + 16 i (16 threads per row: 256 contiguous bytes)
+        const int e = int(threadIdx.x) - 64, ec = e & 15, er = e >> 4;
+        for (; it < seg_end; ++it) {
+          const int64_t j0 = int64_t(it % kb_n) * 64;
+          const bool got = mbar_wait_warp(&z_full[zb], (zph >> zb) & 1u, abort_flag, p.status);
+          float* stg = zst + zb * (kZsRows * kZsLd);
+          if (got) {
+            tc_fence_after();
+            uint32_t r[2][16];
+            const uint32_t zaddr = lane_base + C::kZCol + zb * C::kZBuf + uint32_t(zc0);
+            tmem_ld16_nowait(zaddr, r[0]);
+            tmem_ld16_nowait(zaddr + 16u, r[1]);
+            tmem_wait_ld();
+            tc_fence_before();
+            if (lane == 0) mbar_arrive(&z_empty[zb]);  // the accumulator is in registers now
+            const int l = q * 32 + lane;
+            if (l < kZsRows) {
+              float4* row = reinterpret_cast<float4*>(stg + l * kZsLd + zc0);
+#pragma unroll
+              for (int g = 0; g < 2; ++g)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                  row[4 * g + u] = make_float4(__uint_as_float(r[g][4 * u]), __uint_as_float(r[g][4 * u + 1]),
+                                               __uint_as_float(r[g][4 * u + 2]), __uint_as_float(r[g][4 * u + 3]));
+            }
+          }
+          zph ^= 1u << zb;
+          zb ^= 1u;
+          if (!epi_all(got)) {
+            ok = false;
+            break;
+          }
+          const int64_t j = j0 + 4 * ec;
+#pragma unroll
+          for (int i = 0; i < kZsRows / 16; ++i) {
+            const int l = er + 16 * i;
+            if (l < p.ell2) {
+              const float4 v = *reinterpret_cast<const float4*>(stg + l * kZsLd + 4 * ec);
+              float* zl = p.Z + int64_t(l) * p.ldz + j;
+              if (p.z_vec && j + 4 <= p.n) {
+                red_add_v4(zl, v.x, v.y, v.z, v.w);
+              } else {
+                if (j + 0 < p.n) atomicAdd(zl + 0, v.x);
+                if (j + 1 < p.n) atomicAdd(zl + 1, v.y);
+                if (j + 2 < p.n) atomicAdd(zl + 2, v.z);
+                if (j + 3 < p.n) atomicAdd(zl + 3, v.w);
+              }
+            }
+          }
+        }
+      } else {
       for (; it < seg_end; ++it) {
         const int64_t j0 = int64_t(it % kb_n) * 64 + zc0;  // first column of A this warp reduces
         if (!mbar_wait_warp(&z_full[zb], (zph >> zb) & 1u, abort_flag, p.status)) {
@@ -297,10 +379,14 @@ __global__ void __launch_bounds__(kThreadsD, 1)
         zph ^= 1u << zb;
         zb ^= 1u;
       }
+      }  // ZS
       if (!ok) break;
       // the strip's Y partial (the whole strip when the segment covers all
       // k-blocks): this warp drains the 128-row half `part`
-      if (!mbar_wait_warp(y_full, y_phase, abort_flag, p.status)) break;
+      {
+        const bool got = mbar_wait_warp(y_full, y_phase, abort_flag, p.status);
+        if (ZS ? !epi_all(got) : !got) break;
+      }
       tc_fence_after();
       {
         const int s = part;
@@ -331,11 +417,11 @@ __global__ void __launch_bounds__(kThreadsD, 1)
   }
 }
 
-template <int NCY, int NH>
+template <int NCY, int NH, bool ZS = false>
 void launch_dual(const CUtensorMap& ma, const CUtensorMap& mx, const CUtensorMap& mp, DualParams p, int sms,
                  cudaStream_t s) {
-  using C = DCfg<NCY, NH>;
-  auto kern = dual_bf16_kernel<NCY, NH>;
+  using C = DCfg<NCY, NH, ZS>;
+  auto kern = dual_bf16_kernel<NCY, NH, ZS>;
   static std::atomic<bool> attr_set[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
@@ -377,7 +463,13 @@ void view_dual_bf16(const DualBf16Args& a, cudaStream_t s) {
   CUtensorMap mx = make_map_bf16(a.X, a.n, a.ell1, a.ldx, 64, ncy);
   CUtensorMap mp = make_map_bf16(a.W, a.m, a.ell2, a.ldw, 64, 128);
   const int sms = dev_info(a.device).sms;
-  if (nh == 1) {
+  if (a.ell2 <= kZsRows) {
+    switch (ncy) {
+      case 32: launch_dual<32, 1, true>(ma, mx, mp, p, sms, s); break;
+      case 64: launch_dual<64, 1, true>(ma, mx, mp, p, sms, s); break;
+      default: launch_dual<128, 1, true>(ma, mx, mp, p, sms, s); break;
+    }
+  } else if (nh == 1) {
     switch (ncy) {
       case 32: launch_dual<32, 1>(ma, mx, mp, p, sms, s); break;
       case 64: launch_dual<64, 1>(ma, mx, mp, p, sms, s); break;

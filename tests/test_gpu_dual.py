@@ -48,6 +48,8 @@ def _bf16_matrix(m, n, seed, ld=None):
     (4100, 2056, 128, 256, None),
     (300, 4096, 16, 200, None),
     (1500, 1302, 100, 90, 1304),      # n % 4 != 0: Z (ld n) takes scalar reductions
+    (1500, 1302, 40, 64, 1304),       # staged partial (ell2 <= 64), scalar reductions
+    (2100, 1000, 128, 64, None),      # staged partial beside the widest Y (two stages)
 ])
 def test_fused_dual_sketch_elementwise(m, n, ell1, ell2, ld):
     from paper_1804_07531_gb300._binding import Handle
