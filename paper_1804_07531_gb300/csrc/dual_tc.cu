@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreadsD, 1)
         psi_phase ^= 1u;
         if (!mbar_wait(y_empty, y_phase ^ 1u, abort_flag, p.status)) break;
         tc_fence_after();
-        const uint32_t psi_base = smem_u32(psi);
+        const uint64_t dpsi = sw128_desc(smem_u32(psi), 16, 1024);
         bool first = true;
         for (; it < seg_end; ++it) {
           if (!mbar_wait(&full[stage], phase, abort_flag, p.status)) {
@@ -225,15 +225,17 @@ __global__ void __launch_bounds__(kThreadsD, 1)
           }
           tc_fence_after();
           const uint32_t a_base = smem_u32(ring + stage * C::kStage);
-          const uint32_t x_base = a_base + kATile;
+          const uint64_t da = sw128_desc(a_base, 16, 1024);           // A tile, K-major
+          const uint64_t dx = sw128_desc(a_base + kATile, 16, 1024);  // X tile
+          const uint64_t dam = sw128_desc(a_base, 8192, 1024);        // A tile, MN-major
           // range: Y[s] += A[s] X, K = 64 columns of A in 4 steps of 16
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t bdesc = sw128_desc(x_base + kk * 32, 16, 1024);
+            const uint64_t bdesc = desc_at(dx, kk * 32);
 #pragma unroll
             for (int s = 0; s < 2; ++s)
-              umma_bf16(tmem_base + uint32_t(s * NCY), sw128_desc(a_base + s * 16384 + kk * 32, 16, 1024), bdesc,
-                        kIdY, (first && kk == 0) ? 0u : 1u);
+              umma_bf16(tmem_base + uint32_t(s * NCY), desc_at(da, s * 16384 + kk * 32), bdesc, kIdY,
+                        (first && kk == 0) ? 0u : 1u);
           }
           first = false;
           // co-range: Z^T[zb][h] = Psi[strip][h]^T A, K = the 256 rows in 16 steps
@@ -245,13 +247,12 @@ __global__ void __launch_bounds__(kThreadsD, 1)
           const uint32_t zcol = C::kZCol + zb * C::kZBuf;
 #pragma unroll
           for (int kk = 0; kk < 16; ++kk) {
-            const uint64_t bdesc = sw128_desc(a_base + kk * 2048, 8192, 1024);
+            const uint64_t bdesc = desc_at(dam, kk * 2048);
 #pragma unroll
-            for (int h = 0; h < NH; ++h) {
-              const uint32_t pa = psi_base + ((kk >> 2) * NH + h) * kPsiHalf + (kk & 3) * 32;
-              umma_bf16(tmem_base + zcol + uint32_t(h * 64), sw128_desc(pa, 16, 1024), bdesc, kIdZ,
+            for (int h = 0; h < NH; ++h)
+              umma_bf16(tmem_base + zcol + uint32_t(h * 64),
+                        desc_at(dpsi, ((kk >> 2) * NH + h) * kPsiHalf + (kk & 3) * 32), bdesc, kIdZ,
                         kk == 0 ? 0u : 1u);
-            }
           }
           umma_commit(&z_full[zb]);
           zph ^= 1u << zb;

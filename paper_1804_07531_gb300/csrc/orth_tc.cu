@@ -148,12 +148,13 @@ __device__ __forceinline__ void chunk_stage(uint8_t* ch, const ChunkRegs& cr) {
 // operands: line = column (M or N index), 64 rows per line and box.
 __device__ __forceinline__ void issue_gram(uint32_t tmem, uint32_t ch, bool accumulate) {
   constexpr uint32_t kId = idesc_bf16(128, false);
+  const uint64_t dh0 = sw128_desc(ch, 16, 1024);
 #pragma unroll 1
   for (int s = 0; s < 8; ++s) {
     const uint32_t off = uint32_t(s >> 2) * kBox + uint32_t(s & 3) * 32u;
-    const uint64_t dh = sw128_desc(ch + off, 16, 1024);
-    const uint64_t dm = sw128_desc(ch + kTerm + off, 16, 1024);
-    const uint64_t dl = sw128_desc(ch + 2 * kTerm + off, 16, 1024);
+    const uint64_t dh = desc_at(dh0, off);
+    const uint64_t dm = desc_at(dh0, kTerm + off);
+    const uint64_t dl = desc_at(dh0, 2 * kTerm + off);
     const uint32_t acc = (accumulate || s > 0) ? 1u : 0u;
     umma_bf16(tmem + kColS, dh, dh, kId, acc);  // H^T H
     umma_bf16(tmem + kColS, dm, dm, kId, 1u);   // M^T M
@@ -172,18 +173,20 @@ __host__ __device__ constexpr uint32_t idesc_bf16_bmn(int n) {
 // rows of one half, K = 16 columns per step = 16 lines).
 __device__ __forceinline__ void issue_apply(uint32_t tmem, uint32_t rt, uint32_t ch, int ksteps) {
   constexpr uint32_t kId = idesc_bf16_bmn(64);
+  const uint64_t da0 = sw128_desc(rt, 16, 1024);    // R^{-T} terms, K-major
+  const uint64_t db0 = sw128_desc(ch, 8192, 1024);  // chunk terms, MN-major
 #pragma unroll 1
   for (int s = 0; s < ksteps; ++s) {
     const uint32_t aoff = uint32_t(s >> 2) * kBox + uint32_t(s & 3) * 32u;
-    const uint64_t ah = sw128_desc(rt + aoff, 16, 1024);
-    const uint64_t am = sw128_desc(rt + kTerm + aoff, 16, 1024);
-    const uint64_t al = sw128_desc(rt + 2 * kTerm + aoff, 16, 1024);
+    const uint64_t ah = desc_at(da0, aoff);
+    const uint64_t am = desc_at(da0, kTerm + aoff);
+    const uint64_t al = desc_at(da0, 2 * kTerm + aoff);
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       const uint32_t boff = uint32_t(half) * kBox + uint32_t(s) * 2048u;
-      const uint64_t bh = sw128_desc(ch + boff, 8192, 1024);
-      const uint64_t bm = sw128_desc(ch + kTerm + boff, 8192, 1024);
-      const uint64_t bl = sw128_desc(ch + 2 * kTerm + boff, 8192, 1024);
+      const uint64_t bh = desc_at(db0, boff);
+      const uint64_t bm = desc_at(db0, kTerm + boff);
+      const uint64_t bl = desc_at(db0, 2 * kTerm + boff);
       const uint32_t d = tmem + kColQ + uint32_t(half) * 64u;
       umma_bf16(d, ah, bh, kId, s > 0 ? 1u : 0u);
       umma_bf16(d, ah, bm, kId, 1u);

@@ -86,6 +86,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uin
   d |= 2ull << 61;
   return d;
 }
+// The descriptor of an operand `bytes` past the one d describes (same
+// leading and stride offsets, same swizzle): the start-address field holds
+// address >> 4 in bits 0-13, and shared-memory addresses stay below 2^18, so
+// adding bytes >> 4 (bytes a multiple of 16) never carries out of the field.
+// Loops that issue many MMAs build one descriptor per buffer and step it.
+__device__ __forceinline__ uint64_t desc_at(uint64_t d, uint32_t bytes) { return d + uint64_t(bytes >> 4); }
+
 // Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
 // (bits 7-9, 10-12 = 1), A major (bit 15: 0 K-major, 1 MN-major), B K-major,
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
