@@ -14,12 +14,10 @@
 //   * the Z^T partial of each k-block (double-buffered in TMEM) is added into
 //     Z by the epilogue warps with vector reductions (red.global.add.v4.f32);
 //     Z (n x ell2 FP32) is small enough to stay in L2, so the partials are
-//     reduced there and A is the only operand streamed from HBM.  For
-//     ell2 <= 64 the partial first goes through shared memory (double-
-//     buffered, one barrier of the epilogue warps per k-block), so that each
-//     warp's reduction instruction covers 512 contiguous bytes of Z (two of
-//     its columns) instead of 16 bytes in each of 32 columns: eight times
-//     fewer L2 requests, and every epilogue warp takes a share.
+//     reduced there and A is the only operand streamed from HBM.
+// That form serves ell2 > 64; narrower co-range sketches take the form
+// below the first kernel (128-column k-blocks, the tile as the co-range's M
+// operand).
 // Warp roles: 0 TMA producer, 1 MMA issuer (single thread), 2-9 epilogue
 // (two warps per TMEM lane quarter).
 // Every mbarrier wait is bounded (about 2 s): on expiry the kernel records
@@ -50,40 +48,19 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
 
-// Barrier of the eight epilogue warps (threads 64..319, barrier 1) that also
-// returns whether every one of them passed ok: the warps leave their loop
-// together, so none is left at a later barrier that the others never reach.
-__device__ __forceinline__ bool epi_all(bool ok) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 q, %1, 0;\n\t"
-      "barrier.red.and.pred p, 1, 256, q;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(r)
-      : "r"(ok ? 1u : 0u)
-      : "memory");
-  return r != 0;
-}
-
-constexpr int kZsRows = 64;  // staged Z^T partial: 64 columns of Z (ell2 <= 64)
-constexpr int kZsLd = 68;    // floats per staged row (64 + 4: 16-byte aligned, no bank conflicts)
-
-template <int NCY, int NH, bool ZS>
+template <int NCY, int NH>
 struct DCfg {
   static constexpr uint32_t kXBytes = NCY * 128u;              // NCY rows x 64 BF16
   static constexpr uint32_t kStage = kATile + kXBytes;          // multiple of 1024
   static constexpr uint32_t kPsiBytes = 4u * NH * kPsiHalf;     // 4 K chunks of 64 strip rows
-  static constexpr uint32_t kZsBytes = ZS ? 2u * kZsRows * kZsLd * 4u : 0u;  // two staging buffers
   static constexpr int kStages =
-      int(std::min<size_t>(4, (kSmemMaxD - kPsiBytes - kZsBytes - 2048) / kStage));
-  static constexpr size_t kSmem = size_t(kPsiBytes) + size_t(kStages) * kStage + kZsBytes + 1024 + 256;
+      int(std::min<size_t>(4, (kSmemMaxD - kPsiBytes - 2048) / kStage));
+  static constexpr size_t kSmem = size_t(kPsiBytes) + size_t(kStages) * kStage + 1024 + 256;
   static constexpr uint32_t kZCol = 2 * NCY;                    // TMEM column of Z^T buffer 0
   static constexpr uint32_t kZBuf = NH * 64;                    // TMEM columns per Z^T buffer
   static_assert(kStages >= 2, "at least a double-buffered ring");
   static_assert(kZCol + 2 * kZBuf <= 512, "TMEM holds 512 FP32 columns");
   static_assert(kSmem <= kSmemMaxD, "shared memory");
-  static_assert(!ZS || NH == 1, "the staged partial is one M = 128 half");
 };
 
 struct DualParams {
@@ -99,18 +76,17 @@ struct DualParams {
   int* status;
 };
 
-template <int NCY, int NH, bool ZS>
+template <int NCY, int NH>
 __global__ void __launch_bounds__(kThreadsD, 1)
     dual_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                      const __grid_constant__ CUtensorMap tmP, DualParams p) {
-  using C = DCfg<NCY, NH, ZS>;
+  using C = DCfg<NCY, NH>;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* psi = smem;                                    // [4 chunks][NH halves] 128 x 64 BF16
   uint8_t* ring = smem + C::kPsiBytes;                    // S stages of [A tile | X tile]
-  float* zst = reinterpret_cast<float*>(ring + S * C::kStage);  // [2][kZsRows][kZsLd] (ZS)
-  uint64_t* full = reinterpret_cast<uint64_t*>(ring + S * C::kStage + C::kZsBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + S * C::kStage);
   uint64_t* empty = full + S;
   uint64_t* psi_full = empty + S;
   uint64_t* psi_empty = psi_full + 1;
@@ -290,61 +266,6 @@ __global__ void __launch_bounds__(kThreadsD, 1)
     while (ok && it < it_end) {
       const int strip = int(it / kb_n);
       const int64_t seg_end = std::min<int64_t>(it_end, int64_t(strip + 1) * kb_n);
-      if constexpr (ZS) {
-        // staged: this warp's 32 x 32 piece of the partial (Z columns
-        // q*32 + lane, k-block columns zc0 ..) -> shared memory; after the
-        // barrier, epilogue thread e reduces columns 4 (e % 16) .. + 3 of
-        // rows e / 16 + 16 i (16 threads per row: 256 contiguous bytes)
-        const int e = int(threadIdx.x) - 64, ec = e & 15, er = e >> 4;
-        for (; it < seg_end; ++it) {
-          const int64_t j0 = int64_t(it % kb_n) * 64;
-          const bool got = mbar_wait_warp(&z_full[zb], (zph >> zb) & 1u, abort_flag, p.status);
-          float* stg = zst + zb * (kZsRows * kZsLd);
-          if (got) {
-            tc_fence_after();
-            uint32_t r[2][16];
-            const uint32_t zaddr = lane_base + C::kZCol + zb * C::kZBuf + uint32_t(zc0);
-            tmem_ld16_nowait(zaddr, r[0]);
-            tmem_ld16_nowait(zaddr + 16u, r[1]);
-            tmem_wait_ld();
-            tc_fence_before();
-            if (lane == 0) mbar_arrive(&z_empty[zb]);  // the accumulator is in registers now
-            const int l = q * 32 + lane;
-            if (l < kZsRows) {
-              float4* row = reinterpret_cast<float4*>(stg + l * kZsLd + zc0);
-#pragma unroll
-              for (int g = 0; g < 2; ++g)
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                  row[4 * g + u] = make_float4(__uint_as_float(r[g][4 * u]), __uint_as_float(r[g][4 * u + 1]),
-                                               __uint_as_float(r[g][4 * u + 2]), __uint_as_float(r[g][4 * u + 3]));
-            }
-          }
-          zph ^= 1u << zb;
-          zb ^= 1u;
-          if (!epi_all(got)) {
-            ok = false;
-            break;
-          }
-          const int64_t j = j0 + 4 * ec;
-#pragma unroll
-          for (int i = 0; i < kZsRows / 16; ++i) {
-            const int l = er + 16 * i;
-            if (l < p.ell2) {
-              const float4 v = *reinterpret_cast<const float4*>(stg + l * kZsLd + 4 * ec);
-              float* zl = p.Z + int64_t(l) * p.ldz + j;
-              if (p.z_vec && j + 4 <= p.n) {
-                red_add_v4(zl, v.x, v.y, v.z, v.w);
-              } else {
-                if (j + 0 < p.n) atomicAdd(zl + 0, v.x);
-                if (j + 1 < p.n) atomicAdd(zl + 1, v.y);
-                if (j + 2 < p.n) atomicAdd(zl + 2, v.z);
-                if (j + 3 < p.n) atomicAdd(zl + 3, v.w);
-              }
-            }
-          }
-        }
-      } else {
       for (; it < seg_end; ++it) {
         const int64_t j0 = int64_t(it % kb_n) * 64 + zc0;  // first column of A this warp reduces
         if (!mbar_wait_warp(&z_full[zb], (zph >> zb) & 1u, abort_flag, p.status)) {
@@ -380,14 +301,10 @@ __global__ void __launch_bounds__(kThreadsD, 1)
         zph ^= 1u << zb;
         zb ^= 1u;
       }
-      }  // ZS
       if (!ok) break;
       // the strip's Y partial (the whole strip when the segment covers all
       // k-blocks): this warp drains the 128-row half `part`
-      {
-        const bool got = mbar_wait_warp(y_full, y_phase, abort_flag, p.status);
-        if (ZS ? !epi_all(got) : !got) break;
-      }
+      if (!mbar_wait_warp(y_full, y_phase, abort_flag, p.status)) break;
       tc_fence_after();
       {
         const int s = part;
@@ -418,11 +335,304 @@ __global__ void __launch_bounds__(kThreadsD, 1)
   }
 }
 
-template <int NCY, int NH, bool ZS = false>
+// ------------------------------------------------------------------------
+// Narrow co-range sketches (ell2 <= 64): 128-column k-blocks, and the
+// co-range product with the roles swapped, Z[k-block] (128 columns of A x
+// ell2) = A_tile^T Psi[strip]: the staged tile is the MN-major A operand
+// (M = its 128 columns, two 64-column boxes LBO apart; K = the strip's 256
+// rows) and Psi's strip the K-major B operand (N = 64 lines).  One MMA then
+// covers twice the columns that the Psi-as-A form covers with M = 128 lines
+// of which ell2 <= 64 hold data, so a k-block of 128 columns takes 16
+// range and 16 co-range MMAs where the 64-column form takes 48: the single
+// issuing thread, not HBM, bounded that form.  TMEM lane = column of A, so
+// each epilogue lane adds its column's partials and a warp's reduction
+// instruction covers 32 consecutive floats of a column of Z.
+constexpr uint32_t kAWide = 65536u;     // 256 rows x 128 columns: boxes (r, c) of 128 x 64 at (2r + c) x 16 KB
+constexpr uint32_t kPsiChunkW = 8192u;  // 64 strip rows x 64 ell2-lines BF16
+
+template <int NCY>
+struct WCfg {
+  static constexpr uint32_t kXBytes = 2u * NCY * 128u;       // two boxes of NCY lines x 64 BF16
+  static constexpr uint32_t kStage = kAWide + kXBytes;       // multiple of 1024
+  static constexpr uint32_t kPsiBytes = 4u * kPsiChunkW;     // 4 K chunks of 64 strip rows
+  static constexpr int kStages = int(std::min<size_t>(4, (kSmemMaxD - kPsiBytes - 2048) / kStage));
+  static constexpr size_t kSmem = size_t(kPsiBytes) + size_t(kStages) * kStage + 1024 + 256;
+  static constexpr uint32_t kZCol = 2 * NCY;                 // TMEM column of Z buffer 0
+  static constexpr uint32_t kZBuf = 64;                      // TMEM columns per Z buffer
+  static_assert(kStage % 1024 == 0, "stages keep the 1024-byte swizzle alignment");
+  static_assert(kStages >= 2, "at least a double-buffered ring");
+  static_assert(kZCol + 2 * kZBuf <= 512, "TMEM holds 512 FP32 columns");
+  static_assert(kSmem <= kSmemMaxD, "shared memory");
+};
+
+template <int NCY>
+__global__ void __launch_bounds__(kThreadsD, 1)
+    dual_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
+                     const __grid_constant__ CUtensorMap tmP, DualParams p) {
+  using C = WCfg<NCY>;
+  constexpr int S = C::kStages;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* psi = smem;                  // [4 chunks] 64 lines x 64 BF16
+  uint8_t* ring = smem + C::kPsiBytes;  // S stages of [A boxes | X boxes]
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + S * C::kStage);
+  uint64_t* empty = full + S;
+  uint64_t* psi_full = empty + S;
+  uint64_t* psi_empty = psi_full + 1;
+  uint64_t* y_full = psi_empty + 1;
+  uint64_t* y_empty = y_full + 1;
+  uint64_t* z_full = y_empty + 1;  // [2]
+  uint64_t* z_empty = z_full + 2;  // [2]
+  uint64_t* drain = z_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t G = gridDim.x;
+  const int64_t it_begin = p.iters_total * blockIdx.x / G;
+  const int64_t it_end = p.iters_total * (blockIdx.x + 1) / G;
+  const int kb_n = p.kblocks;  // 128-column k-blocks
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(psi_full, 1);
+    mbar_init(psi_empty, 1);
+    mbar_init(y_full, 1);
+    mbar_init(y_empty, kEpiWarps);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&z_full[b], 1);
+      mbar_init(&z_empty[b], kEpiWarps);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmX)) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmP)) : "memory");
+      uint32_t stage = 0, phase = 0, psi_phase = 0;
+      int64_t it = it_begin;
+      bool ok = true;
+      while (ok && it < it_end) {
+        const int strip = int(it / kb_n);
+        const int64_t seg_end = std::min<int64_t>(it_end, int64_t(strip + 1) * kb_n);
+        // Psi's strip: 4 chunks of 64 rows x 64 lines
+        if (!mbar_wait(psi_empty, psi_phase ^ 1u, abort_flag, p.status)) break;
+        mbar_expect_tx(psi_full, C::kPsiBytes);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tma_load_2d(psi + q * kPsiChunkW, &tmP, psi_full, strip * 256 + q * 64, 0);
+        psi_phase ^= 1u;
+        for (; it < seg_end; ++it) {
+          const int kb = int(it % kb_n);
+          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          uint8_t* sa = ring + stage * C::kStage;
+          mbar_expect_tx(&full[stage], C::kStage);
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+              tma_load_2d(sa + (2 * r + c) * 16384, &tmA, &full[stage], kb * 128 + c * 64, strip * 256 + r * 128);
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+            tma_load_2d(sa + kAWide + c * (NCY * 128), &tmX, &full[stage], kb * 128 + c * 64, 0);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (*abort_flag) {  // let copies already issued land before the CTA exits
+        const uint64_t t0 = globaltimer();
+        while (globaltimer() - t0 < 10000000ull) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t kIdY = idesc_bf16(NCY, false);
+      constexpr uint32_t kIdZ = idesc_bf16(64, true);  // A (the tile) MN-major, N = 64 lines of Psi
+      uint32_t stage = 0, phase = 0, psi_phase = 0, y_phase = 0;
+      uint32_t zb = 0, zph = 0;  // Z buffer, and the phase bit of each buffer
+      int64_t it = it_begin;
+      bool ok = true;
+      while (ok && it < it_end) {
+        const int strip = int(it / kb_n);
+        const int64_t seg_end = std::min<int64_t>(it_end, int64_t(strip + 1) * kb_n);
+        if (!mbar_wait(psi_full, psi_phase, abort_flag, p.status)) break;
+        psi_phase ^= 1u;
+        if (!mbar_wait(y_empty, y_phase ^ 1u, abort_flag, p.status)) break;
+        tc_fence_after();
+        const uint64_t dpsi = sw128_desc(smem_u32(psi), 16, 1024);
+        bool first = true;
+        for (; it < seg_end; ++it) {
+          if (!mbar_wait(&full[stage], phase, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(ring + stage * C::kStage);
+          const uint64_t da = sw128_desc(a_base, 16, 1024);            // A boxes, K-major
+          const uint64_t dx = sw128_desc(a_base + kAWide, 16, 1024);   // X boxes
+          const uint64_t dam = sw128_desc(a_base, 16384, 1024);        // A boxes, MN-major: c = 1 box LBO on
+          // range: Y[r] += A[r] X, K = 128 columns in 8 steps of 16
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t c = uint32_t(kk >> 2), ko = uint32_t(kk & 3) * 32u;
+            const uint64_t bdesc = desc_at(dx, c * (NCY * 128u) + ko);
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+              umma_bf16(tmem_base + uint32_t(r * NCY), desc_at(da, (2u * r + c) * 16384u + ko), bdesc, kIdY,
+                        (first && kk == 0) ? 0u : 1u);
+          }
+          first = false;
+          // co-range: Z[zb] (128 columns x 64 lines) = A_tile^T Psi[strip], K = 256 rows in 16 steps
+          if (!mbar_wait(&z_empty[zb], ((zph >> zb) & 1u) ^ 1u, abort_flag, p.status)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t zcol = C::kZCol + zb * C::kZBuf;
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk)
+            umma_bf16(tmem_base + zcol, desc_at(dam, uint32_t(kk >> 3) * 32768u + uint32_t(kk & 7) * 2048u),
+                      desc_at(dpsi, uint32_t(kk >> 2) * kPsiChunkW + uint32_t(kk & 3) * 32u), kIdZ,
+                      kk == 0 ? 0u : 1u);
+          umma_commit(&z_full[zb]);
+          zph ^= 1u << zb;
+          zb ^= 1u;
+          umma_commit(&empty[stage]);
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(y_full);
+        y_phase ^= 1u;
+        umma_commit(psi_empty);
+      }
+      umma_commit(drain);
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else {
+    // --------------------------------------------------------- epilogue
+    // Warps 2..9: warp w reads TMEM lane quarter q = w % 4; the two warps of
+    // a quarter take Z lines 0-31 and 32-63 (part), and the two 128-row
+    // halves of Y.
+    const int q = warp & 3, part = (warp - 2) >> 2;
+    const uint32_t lane_base = tmem_base + (uint32_t(q * 32) << 16);
+    uint32_t y_phase = 0, zb = 0, zph = 0;
+    int64_t it = it_begin;
+    bool ok = true;
+    while (ok && it < it_end) {
+      const int strip = int(it / kb_n);
+      const int64_t seg_end = std::min<int64_t>(it_end, int64_t(strip + 1) * kb_n);
+      for (; it < seg_end; ++it) {
+        const int64_t j = int64_t(it % kb_n) * 128 + q * 32 + lane;  // the column of A this lane adds
+        if (!mbar_wait_warp(&z_full[zb], (zph >> zb) & 1u, abort_flag, p.status)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        uint32_t r[2][16];
+        const uint32_t zaddr = lane_base + C::kZCol + zb * C::kZBuf + uint32_t(part * 32);
+        tmem_ld16_nowait(zaddr, r[0]);
+        tmem_ld16_nowait(zaddr + 16u, r[1]);
+        tmem_wait_ld();
+        tc_fence_before();
+        if (lane == 0) mbar_arrive(&z_empty[zb]);  // the accumulator is in registers now
+        if (j < p.n) {
+          float* zj = p.Z + j;
+#pragma unroll
+          for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int l = part * 32 + g * 16 + u;
+              if (l < p.ell2) atomicAdd(zj + int64_t(l) * p.ldz, __uint_as_float(r[g][u]));
+            }
+        }
+        zph ^= 1u << zb;
+        zb ^= 1u;
+      }
+      if (!ok) break;
+      // the strip's Y partial: this warp drains the 128-row half `part`
+      if (!mbar_wait_warp(y_full, y_phase, abort_flag, p.status)) break;
+      tc_fence_after();
+      {
+        const int s = part;
+        const int64_t row = int64_t(strip) * 256 + s * 128 + q * 32 + lane;
+        const bool row_ok = row < p.m;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NCY; c0 += 16) {
+          float v[16];
+          tmem_ld16(lane_base + uint32_t(s * NCY + c0), v);
+          if (row_ok) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+              if (c0 + u < p.ell1) atomicAdd(p.Y + row + int64_t(c0 + u) * p.ldy, v[u]);
+          }
+        }
+      }
+      tc_fence_before();
+      if (lane == 0) mbar_arrive(y_empty);
+      y_phase ^= 1u;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512));
+  }
+}
+
+template <int NCY>
+void launch_wide(const CUtensorMap& ma, const CUtensorMap& mx, const CUtensorMap& mp, DualParams p, int sms,
+                 cudaStream_t s) {
+  using C = WCfg<NCY>;
+  auto kern = dual_wide_kernel<NCY>;
+  static std::atomic<bool> attr_set[64];  // attributes set, per device
+  int dev = 0;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  if (!attr_set[dev & 63]) {
+    LR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(C::kSmem)));
+    attr_set[dev & 63] = true;
+  }
+  const int grid = int(std::min<int64_t>(sms, p.iters_total));
+  if (grid <= 0) return;
+  kern<<<grid, kThreadsD, C::kSmem, s>>>(ma, mx, mp, p);
+  LR_LAUNCH_CHECK();
+}
+
+template <int NCY, int NH>
 void launch_dual(const CUtensorMap& ma, const CUtensorMap& mx, const CUtensorMap& mp, DualParams p, int sms,
                  cudaStream_t s) {
-  using C = DCfg<NCY, NH, ZS>;
-  auto kern = dual_bf16_kernel<NCY, NH, ZS>;
+  using C = DCfg<NCY, NH>;
+  auto kern = dual_bf16_kernel<NCY, NH>;
   static std::atomic<bool> attr_set[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
@@ -464,11 +674,15 @@ void view_dual_bf16(const DualBf16Args& a, cudaStream_t s) {
   CUtensorMap mx = make_map_bf16(a.X, a.n, a.ell1, a.ldx, 64, ncy);
   CUtensorMap mp = make_map_bf16(a.W, a.m, a.ell2, a.ldw, 64, 128);
   const int sms = dev_info(a.device).sms;
-  if (a.ell2 <= kZsRows) {
+  if (a.ell2 <= 64) {
+    // 128-column k-blocks, co-range with the tile as the M operand
+    p.kblocks = ceil_div(a.n, 128);
+    p.iters_total = int64_t(ceil_div(a.m, 256)) * p.kblocks;
+    CUtensorMap mpw = make_map_bf16(a.W, a.m, a.ell2, a.ldw, 64, 64);
     switch (ncy) {
-      case 32: launch_dual<32, 1, true>(ma, mx, mp, p, sms, s); break;
-      case 64: launch_dual<64, 1, true>(ma, mx, mp, p, sms, s); break;
-      default: launch_dual<128, 1, true>(ma, mx, mp, p, sms, s); break;
+      case 32: launch_wide<32>(ma, mx, mpw, p, sms, s); break;
+      case 64: launch_wide<64>(ma, mx, mpw, p, sms, s); break;
+      default: launch_wide<128>(ma, mx, mpw, p, sms, s); break;
     }
   } else if (nh == 1) {
     switch (ncy) {

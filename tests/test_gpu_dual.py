@@ -5,10 +5,11 @@ staged tile of A feeds both products.  Checked element by element against the
 FP64 products of the same BF16 values (max_i |y_ij - ref_ij| <= 2e-5
 max_i |ref_ij| in every column j: FP32 accumulation over K terms), at shapes
 with a ragged last strip (m not a multiple of 256), a ragged last k-block (n
-not a multiple of 64), ell2 on both sides of 128, and a Z whose leading
-dimension forbids vector reductions; and against the two-pass form
-(opts.band_mb = -1) on the same inputs.  The default picks the fused kernel
-for ell2 <= 64 (checked by the launch trace).
+not a multiple of 64 or of 128), ell2 on both sides of 64 (the narrow form
+with 128-column k-blocks) and of 128, and a Z whose leading dimension forbids
+vector reductions; and against the two-pass form (opts.band_mb = -1) on the
+same inputs.  The default picks the fused kernel for ell2 <= 64 (checked by
+the launch trace).
 """
 import numpy as np
 import pytest
@@ -48,8 +49,8 @@ def _bf16_matrix(m, n, seed, ld=None):
     (4100, 2056, 128, 256, None),
     (300, 4096, 16, 200, None),
     (1500, 1302, 100, 90, 1304),      # n % 4 != 0: Z (ld n) takes scalar reductions
-    (1500, 1302, 40, 64, 1304),       # staged partial (ell2 <= 64), scalar reductions
-    (2100, 1000, 128, 64, None),      # staged partial beside the widest Y (two stages)
+    (1500, 1302, 40, 64, 1304),       # narrow co-range form (ell2 <= 64), ragged 128-column k-blocks
+    (2100, 1000, 128, 64, None),      # narrow co-range form beside the widest Y
 ])
 def test_fused_dual_sketch_elementwise(m, n, ell1, ell2, ld):
     from paper_1804_07531_gb300._binding import Handle
