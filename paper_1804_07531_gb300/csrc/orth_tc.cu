@@ -169,32 +169,30 @@ __host__ __device__ constexpr uint32_t idesc_bf16_bmn(int n) {
 }
 
 // Q_ch^T = R^{-T} Y_ch^T (thread 0 issues): A = R^{-T} (K-major: line = output
-// column, K = the block's columns), B = the staged chunk, MN-major (N = 64
-// rows of one half, K = 16 columns per step = 16 lines).
+// column, K = the block's columns), B = the staged chunk, MN-major (N = its
+// 128 rows: the two 64-row halves, one box apart as the leading offset;
+// K = 16 columns per step = 16 lines).  One MMA per product and step.
 __device__ __forceinline__ void issue_apply(uint32_t tmem, uint32_t rt, uint32_t ch, int ksteps) {
-  constexpr uint32_t kId = idesc_bf16_bmn(64);
+  constexpr uint32_t kId = idesc_bf16_bmn(128);
   const uint64_t da0 = sw128_desc(rt, 16, 1024);    // R^{-T} terms, K-major
-  const uint64_t db0 = sw128_desc(ch, 8192, 1024);  // chunk terms, MN-major
+  const uint64_t db0 = sw128_desc(ch, kBox, 1024);  // chunk terms, MN-major, halves kBox apart
+  const uint32_t d = tmem + kColQ;
 #pragma unroll 1
   for (int s = 0; s < ksteps; ++s) {
     const uint32_t aoff = uint32_t(s >> 2) * kBox + uint32_t(s & 3) * 32u;
     const uint64_t ah = desc_at(da0, aoff);
     const uint64_t am = desc_at(da0, kTerm + aoff);
     const uint64_t al = desc_at(da0, 2 * kTerm + aoff);
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const uint32_t boff = uint32_t(half) * kBox + uint32_t(s) * 2048u;
-      const uint64_t bh = desc_at(db0, boff);
-      const uint64_t bm = desc_at(db0, kTerm + boff);
-      const uint64_t bl = desc_at(db0, 2 * kTerm + boff);
-      const uint32_t d = tmem + kColQ + uint32_t(half) * 64u;
-      umma_bf16(d, ah, bh, kId, s > 0 ? 1u : 0u);
-      umma_bf16(d, ah, bm, kId, 1u);
-      umma_bf16(d, am, bh, kId, 1u);
-      umma_bf16(d, ah, bl, kId, 1u);
-      umma_bf16(d, al, bh, kId, 1u);
-      umma_bf16(d, am, bm, kId, 1u);
-    }
+    const uint32_t boff = uint32_t(s) * 2048u;
+    const uint64_t bh = desc_at(db0, boff);
+    const uint64_t bm = desc_at(db0, kTerm + boff);
+    const uint64_t bl = desc_at(db0, 2 * kTerm + boff);
+    umma_bf16(d, ah, bh, kId, s > 0 ? 1u : 0u);
+    umma_bf16(d, ah, bm, kId, 1u);
+    umma_bf16(d, am, bh, kId, 1u);
+    umma_bf16(d, ah, bl, kId, 1u);
+    umma_bf16(d, al, bh, kId, 1u);
+    umma_bf16(d, am, bm, kId, 1u);
   }
 }
 

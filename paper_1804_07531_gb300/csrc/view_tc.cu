@@ -152,14 +152,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t a_base = smem_u32(smem + stage * C::kStage);
-          const uint32_t b_base = a_base + C::kABytes;
+          const uint64_t da = (MODE == 0) ? sw128_desc(a_base, 16, 1024) : sw128_desc(a_base, 8192, 1024);
+          const uint64_t db = sw128_desc(a_base + C::kABytes, 16, 1024);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t bdesc = sw128_desc(b_base + kk * 32, 16, 1024);
+            const uint64_t bdesc = desc_at(db, kk * 32);
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-              const uint64_t adesc = (MODE == 0) ? sw128_desc(a_base + s * 16384 + kk * 32, 16, 1024)
-                                                 : sw128_desc(a_base + s * 16384 + kk * 2048, 8192, 1024);
+              const uint64_t adesc = desc_at(da, s * 16384 + (MODE == 0 ? kk * 32 : kk * 2048));
               umma_bf16(tmem_base + uint32_t(s * NCOL), adesc, bdesc, kIdesc, (first && kk == 0) ? 0u : 1u);
             }
           }
@@ -360,14 +360,16 @@ __global__ void __launch_bounds__(kThreadsT, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t ah = smem_u32(a_hi(stage)), al = smem_u32(a_lo(stage));
-          const uint32_t bh = smem_u32(b_hi(stage)), bl = smem_u32(b_lo(stage));
+          const uint64_t dah0 = sw128_desc(smem_u32(a_hi(stage)), 16, 1024);
+          const uint64_t dal0 = sw128_desc(smem_u32(a_lo(stage)), 16, 1024);
+          const uint64_t dbh0 = sw128_desc(smem_u32(b_hi(stage)), 16, 1024);
+          const uint64_t dbl0 = sw128_desc(smem_u32(b_lo(stage)), 16, 1024);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t dbh = sw128_desc(bh + kk * 32, 16, 1024);
-            const uint64_t dbl = sw128_desc(bl + kk * 32, 16, 1024);
-            const uint64_t dah = sw128_desc(ah + kk * 32, 16, 1024);
-            const uint64_t dal = sw128_desc(al + kk * 32, 16, 1024);
+            const uint64_t dbh = desc_at(dbh0, kk * 32);
+            const uint64_t dbl = desc_at(dbl0, kk * 32);
+            const uint64_t dah = desc_at(dah0, kk * 32);
+            const uint64_t dal = desc_at(dal0, kk * 32);
             umma_tf32(tmem_base, dah, dbh, kIdesc, (first && kk == 0) ? 0u : 1u);
             umma_tf32(tmem_base, dah, dbl, kIdesc, 1u);
             umma_tf32(tmem_base, dal, dbh, kIdesc, 1u);
