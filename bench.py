@@ -185,13 +185,13 @@ def _peaks():
 
 
 # ------------------------------------------------------- dual sketch
-DUAL_WIDTHS = ((32, 64), (120, 240))
+DUAL_WIDTHS = ((32, 64), (64, 128), (120, 240))
 
 
 def dual_sketch_cases(a, hbm, bf16_pk, reps=10):
     """The one-read dual sketch Y = A X, Z = A^T W (Alg. 7 steps a, b) on the
     workload's matrix: the fused kernel (each staged tile of A feeds both
-    products, A read once) against two full passes, at a narrow width pair
+    products, A read once) against two full passes, at two narrow width pairs
     and at the single-pass workload's (ell1, ell2) = (120, 240).  Kernel times
     come from the library's CUDA-event trace; call times include the operand
     conversion and output zeroing."""
@@ -208,7 +208,7 @@ def dual_sketch_cases(a, hbm, bf16_pk, reps=10):
     for ell1, ell2 in DUAL_WIDTHS:
         x = torch.randn(n, ell1, generator=gen, device=a.device)
         w = torch.randn(m, ell2, generator=gen, device=a.device)
-        res = {"default": "fused" if ell2 <= 64 else "two_pass"}
+        res = {"default": "fused" if ell2 <= 64 or (ell2 <= 128 and ell1 <= 64) else "two_pass"}
         flops = 2.0 * m * n * (ell1 + ell2)
         for name, band in (("fused", -2), ("two_pass", -1)):
             for _ in range(2):

@@ -91,9 +91,10 @@ typedef struct {
                                plain passes; without it such a sketch ends in
                                LR_ERR_BREAKDOWN */
   int32_t band_mb;          /* one-read sketches (dual, chained): 0 = default: the dual
-                               sketch of a BF16 A with ell1 <= 128 and ell2 <= 64 runs the
-                               fused kernel that feeds each staged tile of A to both
-                               products (A read once), other widths two full passes;
+                               sketch of a BF16 A with ell1 <= 128 and ell2 <= 64, or
+                               ell1 <= 64 and ell2 <= 128, runs the fused kernel that
+                               feeds each staged tile of A to both products (A read
+                               once), other widths two full passes;
                                -2 = the fused kernel whenever ell1 <= 128, ell2 <= 256;
                                -1 = two full passes; > 0 = L2 bands of that many MiB of
                                A, each read by the two products back to back */

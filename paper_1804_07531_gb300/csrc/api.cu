@@ -346,9 +346,11 @@ void view_corange(Ctx& c, const AMat& A, const Mat& W, Mat Z, bool last = false)
 // each staged tile feeding both products; it flushes a partial Z^T per tile
 // of 256 rows, ell2 / 64 bytes of L2 reductions per element of A, which L2
 // absorbs at about the HBM rate (measured), so it wins where that is below
-// the 2 bytes of the second read it saves: by default it runs for
-// ell2 <= 64 (and ell1 <= 128); opts.band_mb = -2 forces it (ell2 <= 256),
-// -1 forces two passes.  Otherwise the range and co-range kernels sweep the
+// the 2 bytes of the second read it saves.  Its narrow form (128-column
+// k-blocks, ell2 <= 64, or ell2 <= 128 with ell1 <= 64) halves those
+// reductions and measured faster than two passes at both widths, so by
+// default it runs there; opts.band_mb = -2 forces the fused kernel
+// (ell1 <= 128, ell2 <= 256), -1 forces two passes.  Otherwise the range and co-range kernels sweep the
 // bands of band_rows() (by default one band: two full passes over A).
 void view_dual(Ctx& c, const AMat& A, const Mat& X, Mat Y, const Mat& W, Mat Z) {
   ArenaScope sc(c.ar);
@@ -358,7 +360,8 @@ void view_dual(Ctx& c, const AMat& A, const Mat& X, Mat Y, const Mat& W, Mat Z) 
   zero_f32(Y.p, Y.rows, Y.cols, Y.ld, c.s);
   zero_f32(Z.p, Z.rows, Z.cols, Z.ld, c.s);
   const bool fused = A.bf16 && dual_bf16_supported(int(X.cols), int(W.cols)) &&
-                     (c.opt.band_mb == -2 || (c.opt.band_mb == 0 && W.cols <= 64));
+                     (c.opt.band_mb == -2 ||
+                      (c.opt.band_mb == 0 && (W.cols <= 64 || (W.cols <= 128 && X.cols <= 64))));
   if (fused) {
     TraceScope tr(c, LR_TRACE_VIEW_DUAL);
     DualBf16Args d;

@@ -348,32 +348,33 @@ __global__ void __launch_bounds__(kThreadsD, 1)
 // each epilogue lane adds its column's partials and a warp's reduction
 // instruction covers 32 consecutive floats of a column of Z.
 constexpr uint32_t kAWide = 65536u;     // 256 rows x 128 columns: boxes (r, c) of 128 x 64 at (2r + c) x 16 KB
-constexpr uint32_t kPsiChunkW = 8192u;  // 64 strip rows x 64 ell2-lines BF16
 
-template <int NCY>
+// NZ: Psi lines held (the co-range MMA's N), 64 or 128.
+template <int NCY, int NZ>
 struct WCfg {
   static constexpr uint32_t kXBytes = 2u * NCY * 128u;       // two boxes of NCY lines x 64 BF16
   static constexpr uint32_t kStage = kAWide + kXBytes;       // multiple of 1024
-  static constexpr uint32_t kPsiBytes = 4u * kPsiChunkW;     // 4 K chunks of 64 strip rows
+  static constexpr uint32_t kPsiChunk = NZ * 128u;           // 64 strip rows x NZ lines BF16
+  static constexpr uint32_t kPsiBytes = 4u * kPsiChunk;      // 4 K chunks of 64 strip rows
   static constexpr int kStages = int(std::min<size_t>(4, (kSmemMaxD - kPsiBytes - 2048) / kStage));
   static constexpr size_t kSmem = size_t(kPsiBytes) + size_t(kStages) * kStage + 1024 + 256;
   static constexpr uint32_t kZCol = 2 * NCY;                 // TMEM column of Z buffer 0
-  static constexpr uint32_t kZBuf = 64;                      // TMEM columns per Z buffer
+  static constexpr uint32_t kZBuf = NZ;                      // TMEM columns per Z buffer
   static_assert(kStage % 1024 == 0, "stages keep the 1024-byte swizzle alignment");
   static_assert(kStages >= 2, "at least a double-buffered ring");
   static_assert(kZCol + 2 * kZBuf <= 512, "TMEM holds 512 FP32 columns");
   static_assert(kSmem <= kSmemMaxD, "shared memory");
 };
 
-template <int NCY>
+template <int NCY, int NZ>
 __global__ void __launch_bounds__(kThreadsD, 1)
     dual_wide_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                      const __grid_constant__ CUtensorMap tmP, DualParams p) {
-  using C = WCfg<NCY>;
+  using C = WCfg<NCY, NZ>;
   constexpr int S = C::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* psi = smem;                  // [4 chunks] 64 lines x 64 BF16
+  uint8_t* psi = smem;                  // [4 chunks] NZ lines x 64 BF16
   uint8_t* ring = smem + C::kPsiBytes;  // S stages of [A boxes | X boxes]
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + S * C::kStage);
   uint64_t* empty = full + S;
@@ -433,11 +434,11 @@ __global__ void __launch_bounds__(kThreadsD, 1)
       while (ok && it < it_end) {
         const int strip = int(it / kb_n);
         const int64_t seg_end = std::min<int64_t>(it_end, int64_t(strip + 1) * kb_n);
-        // Psi's strip: 4 chunks of 64 rows x 64 lines
+        // Psi's strip: 4 chunks of 64 rows x NZ lines
         if (!mbar_wait(psi_empty, psi_phase ^ 1u, abort_flag, p.status)) break;
         mbar_expect_tx(psi_full, C::kPsiBytes);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) tma_load_2d(psi + q * kPsiChunkW, &tmP, psi_full, strip * 256 + q * 64, 0);
+        for (int q = 0; q < 4; ++q) tma_load_2d(psi + q * C::kPsiChunk, &tmP, psi_full, strip * 256 + q * 64, 0);
         psi_phase ^= 1u;
         for (; it < seg_end; ++it) {
           const int kb = int(it % kb_n);
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(kThreadsD, 1)
     // ------------------------------------------------------- MMA issuer
     if (lane == 0) {
       constexpr uint32_t kIdY = idesc_bf16(NCY, false);
-      constexpr uint32_t kIdZ = idesc_bf16(64, true);  // A (the tile) MN-major, N = 64 lines of Psi
+      constexpr uint32_t kIdZ = idesc_bf16(NZ, true);  // A (the tile) MN-major, N = NZ lines of Psi
       uint32_t stage = 0, phase = 0, psi_phase = 0, y_phase = 0;
       uint32_t zb = 0, zph = 0;  // Z buffer, and the phase bit of each buffer
       int64_t it = it_begin;
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(kThreadsD, 1)
                         (first && kk == 0) ? 0u : 1u);
           }
           first = false;
-          // co-range: Z[zb] (128 columns x 64 lines) = A_tile^T Psi[strip], K = 256 rows in 16 steps
+          // co-range: Z[zb] (128 columns x NZ lines) = A_tile^T Psi[strip], K = 256 rows in 16 steps
           if (!mbar_wait(&z_empty[zb], ((zph >> zb) & 1u) ^ 1u, abort_flag, p.status)) {
             ok = false;
             break;
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(kThreadsD, 1)
 #pragma unroll
           for (int kk = 0; kk < 16; ++kk)
             umma_bf16(tmem_base + zcol, desc_at(dam, uint32_t(kk >> 3) * 32768u + uint32_t(kk & 7) * 2048u),
-                      desc_at(dpsi, uint32_t(kk >> 2) * kPsiChunkW + uint32_t(kk & 3) * 32u), kIdZ,
+                      desc_at(dpsi, uint32_t(kk >> 2) * C::kPsiChunk + uint32_t(kk & 3) * 32u), kIdZ,
                       kk == 0 ? 0u : 1u);
           umma_commit(&z_full[zb]);
           zph ^= 1u << zb;
@@ -557,20 +558,21 @@ __global__ void __launch_bounds__(kThreadsD, 1)
           break;
         }
         tc_fence_after();
-        uint32_t r[2][16];
-        const uint32_t zaddr = lane_base + C::kZCol + zb * C::kZBuf + uint32_t(part * 32);
-        tmem_ld16_nowait(zaddr, r[0]);
-        tmem_ld16_nowait(zaddr + 16u, r[1]);
+        constexpr int kG = NZ / 32;  // 16-line groups this warp drains
+        uint32_t r[kG][16];
+        const uint32_t zaddr = lane_base + C::kZCol + zb * C::kZBuf + uint32_t(part * (NZ / 2));
+#pragma unroll
+        for (int g = 0; g < kG; ++g) tmem_ld16_nowait(zaddr + uint32_t(16 * g), r[g]);
         tmem_wait_ld();
         tc_fence_before();
         if (lane == 0) mbar_arrive(&z_empty[zb]);  // the accumulator is in registers now
         if (j < p.n) {
           float* zj = p.Z + j;
 #pragma unroll
-          for (int g = 0; g < 2; ++g)
+          for (int g = 0; g < kG; ++g)
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-              const int l = part * 32 + g * 16 + u;
+              const int l = part * (NZ / 2) + g * 16 + u;
               if (l < p.ell2) atomicAdd(zj + int64_t(l) * p.ldz, __uint_as_float(r[g][u]));
             }
         }
@@ -610,11 +612,11 @@ __global__ void __launch_bounds__(kThreadsD, 1)
   }
 }
 
-template <int NCY>
+template <int NCY, int NZ>
 void launch_wide(const CUtensorMap& ma, const CUtensorMap& mx, const CUtensorMap& mp, DualParams p, int sms,
                  cudaStream_t s) {
-  using C = WCfg<NCY>;
-  auto kern = dual_wide_kernel<NCY>;
+  using C = WCfg<NCY, NZ>;
+  auto kern = dual_wide_kernel<NCY, NZ>;
   static std::atomic<bool> attr_set[64];  // attributes set, per device
   int dev = 0;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
@@ -674,15 +676,23 @@ void view_dual_bf16(const DualBf16Args& a, cudaStream_t s) {
   CUtensorMap mx = make_map_bf16(a.X, a.n, a.ell1, a.ldx, 64, ncy);
   CUtensorMap mp = make_map_bf16(a.W, a.m, a.ell2, a.ldw, 64, 128);
   const int sms = dev_info(a.device).sms;
-  if (a.ell2 <= 64) {
+  if (a.ell2 <= 64 || (a.ell2 <= 128 && ncy <= 64)) {
     // 128-column k-blocks, co-range with the tile as the M operand
     p.kblocks = ceil_div(a.n, 128);
     p.iters_total = int64_t(ceil_div(a.m, 256)) * p.kblocks;
-    CUtensorMap mpw = make_map_bf16(a.W, a.m, a.ell2, a.ldw, 64, 64);
-    switch (ncy) {
-      case 32: launch_wide<32>(ma, mx, mpw, p, sms, s); break;
-      case 64: launch_wide<64>(ma, mx, mpw, p, sms, s); break;
-      default: launch_wide<128>(ma, mx, mpw, p, sms, s); break;
+    const int nz = a.ell2 <= 64 ? 64 : 128;
+    CUtensorMap mpw = make_map_bf16(a.W, a.m, a.ell2, a.ldw, 64, nz);
+    if (nz == 64) {
+      switch (ncy) {
+        case 32: launch_wide<32, 64>(ma, mx, mpw, p, sms, s); break;
+        case 64: launch_wide<64, 64>(ma, mx, mpw, p, sms, s); break;
+        default: launch_wide<128, 64>(ma, mx, mpw, p, sms, s); break;
+      }
+    } else {
+      switch (ncy) {
+        case 32: launch_wide<32, 128>(ma, mx, mpw, p, sms, s); break;
+        default: launch_wide<64, 128>(ma, mx, mpw, p, sms, s); break;
+      }
     }
   } else if (nh == 1) {
     switch (ncy) {

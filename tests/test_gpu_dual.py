@@ -8,8 +8,8 @@ with a ragged last strip (m not a multiple of 256), a ragged last k-block (n
 not a multiple of 64 or of 128), ell2 on both sides of 64 (the narrow form
 with 128-column k-blocks) and of 128, and a Z whose leading dimension forbids
 vector reductions; and against the two-pass form (opts.band_mb = -1) on the
-same inputs.  The default picks the fused kernel for ell2 <= 64 (checked by
-the launch trace).
+same inputs.  The default picks the fused kernel for ell2 <= 64, and for
+ell2 <= 128 when ell1 <= 64 (checked by the launch trace).
 """
 import numpy as np
 import pytest
@@ -51,6 +51,8 @@ def _bf16_matrix(m, n, seed, ld=None):
     (1500, 1302, 100, 90, 1304),      # n % 4 != 0: Z (ld n) takes scalar reductions
     (1500, 1302, 40, 64, 1304),       # narrow co-range form (ell2 <= 64), ragged 128-column k-blocks
     (2100, 1000, 128, 64, None),      # narrow co-range form beside the widest Y
+    (1000, 704, 60, 120, None),       # the same form with 128 lines of Psi
+    (1500, 1302, 40, 100, 1304),      # ... ragged, scalar reductions
 ])
 def test_fused_dual_sketch_elementwise(m, n, ell1, ell2, ld):
     from paper_1804_07531_gb300._binding import Handle
@@ -103,12 +105,12 @@ def test_default_picks_fused_kernel_for_narrow_sketches_only():
     a = _bf16_matrix(1024, 768, 5)
     h = Handle.get(0)
     h.set_trace(True)
-    for ell2, want in ((64, 1), (65, 0)):
-        x = torch.randn(768, 32, device=DEV)
+    for ell1, ell2, want in ((32, 64, 1), (64, 128, 1), (65, 128, 0), (32, 129, 0)):
+        x = torch.randn(768, ell1, device=DEV)
         w = torch.randn(1024, ell2, device=DEV)
         h.trace_read("view_dual", reset=True)
         api().sketch(a, x, w)
         _, launches = h.trace_read("view_dual", reset=True)
-        assert launches == want, (ell2, launches)
+        assert launches == want, (ell1, ell2, launches)
     h.set_trace(False)
     assert api().device_status(0) == 0
