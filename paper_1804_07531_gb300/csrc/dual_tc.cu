@@ -15,9 +15,9 @@
 //     Z by the epilogue warps with vector reductions (red.global.add.v4.f32);
 //     Z (n x ell2 FP32) is small enough to stay in L2, so the partials are
 //     reduced there and A is the only operand streamed from HBM.
-// That form serves ell2 > 64; narrower co-range sketches take the form
-// below the first kernel (128-column k-blocks, the tile as the co-range's M
-// operand).
+// That form serves the widths the narrow form below cannot hold (ell2 > 128,
+// or ell2 > 64 with ell1 > 64); the narrow form takes 128-column k-blocks and
+// the tile as the co-range's M operand.
 // Warp roles: 0 TMA producer, 1 MMA issuer (single thread), 2-9 epilogue
 // (two warps per TMEM lane quarter).
 // Every mbarrier wait is bounded (about 2 s): on expiry the kernel records
@@ -336,15 +336,16 @@ __global__ void __launch_bounds__(kThreadsD, 1)
 }
 
 // ------------------------------------------------------------------------
-// Narrow co-range sketches (ell2 <= 64): 128-column k-blocks, and the
-// co-range product with the roles swapped, Z[k-block] (128 columns of A x
-// ell2) = A_tile^T Psi[strip]: the staged tile is the MN-major A operand
-// (M = its 128 columns, two 64-column boxes LBO apart; K = the strip's 256
-// rows) and Psi's strip the K-major B operand (N = 64 lines).  One MMA then
-// covers twice the columns that the Psi-as-A form covers with M = 128 lines
-// of which ell2 <= 64 hold data, so a k-block of 128 columns takes 16
-// range and 16 co-range MMAs where the 64-column form takes 48: the single
-// issuing thread, not HBM, bounded that form.  TMEM lane = column of A, so
+// Narrow co-range sketches (ell2 <= 64, or ell2 <= 128 with ell1 <= 64, so
+// that Psi's strip and two stages fit shared memory): 128-column k-blocks,
+// and the co-range product with the roles swapped, Z[k-block] (128 columns
+// of A x ell2) = A_tile^T Psi[strip]: the staged tile is the MN-major A
+// operand (M = its 128 columns, two 64-column boxes LBO apart; K = the
+// strip's 256 rows) and Psi's strip the K-major B operand (N = NZ = 64 or
+// 128 lines).  One MMA then covers twice the columns of the Psi-as-A form
+// (M = 128 lines, N = 64 columns), so a k-block of 128 columns takes 16
+// range and 16 co-range MMAs where the 64-column form takes 48 (ell2 <= 64):
+// the single issuing thread, not HBM, bounded that form.  TMEM lane = column of A, so
 // each epilogue lane adds its column's partials and a warp's reduction
 // instruction covers 32 consecutive floats of a column of Z.
 constexpr uint32_t kAWide = 65536u;     // 256 rows x 128 columns: boxes (r, c) of 128 x 64 at (2r + c) x 16 KB
