@@ -950,10 +950,21 @@ void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat&
   float* W = c.ar.take<float>(size_t(Lk) * Lk);
   float* Vj = c.ar.take<float>(size_t(Lk) * Lk);
   float* Sv = c.ar.take<float>(size_t(Lk));
+  // The last view A Q_r starts with A times K's first block, which the
+  // second chained view forms as its Y: that view writes F's first block,
+  // whose thin QR (with its R) serves both that step and F's QR, and the
+  // last view runs over K's later blocks (not with split_last, whose last
+  // view is the more accurate two-term one over all of K).
+  const bool reuse = !c.opt.split_last && v >= 3;
   Mat x = Om;
   for (int i = 1; i <= v - 1; ++i) {
-    view_chained(c, A, x, Y, Z);         // Y = A X, Z = A^T Y from one read
-    orth(c, Y, Rc);                      // Y = Q_c R_c
+    const bool f_blk = reuse && i == 2;  // Y = A K_0, F's first block
+    Mat Yi = f_blk ? Mat{F.p, A.m, ell, A.m} : Y;
+    view_chained(c, A, x, Yi, Z);        // Y = A X, Z = A^T Y from one read
+    orth(c, Yi, f_blk ? Rf : Rc, 0, false, f_blk ? Lk : 0);  // Y = Q_c R_c
+    if (f_blk && !c.measure)
+      LR_CHECK_CUDA(cudaMemcpy2DAsync(Rc, size_t(ell) * sizeof(double), Rf, size_t(Lk) * sizeof(double),
+                                      size_t(ell) * sizeof(double), size_t(ell), cudaMemcpyDeviceToDevice, c.s));
     Mat blk{K.col(int64_t(i - 1) * ell), A.n, ell, A.n};
     tri_inv_any(c, Rc, ell, Ri);
     if (!c.measure) {
@@ -963,8 +974,9 @@ void run_krylov_rowwise(Ctx& c, const AMat& A, int k, int ell, int v, const Mat&
     x = blk;
   }
   orth(c, K, nullptr, v >= 3 ? ell : 0);  // Q_r = qr(K_r), first block already orthonormal
-  view_range(c, A, K, F, true);          // last view: A Q_r
-  orth(c, F, Rf);
+  const int f0 = reuse ? ell : 0;
+  view_range(c, A, Mat{K.col(f0), A.n, Lk - f0, A.n}, Mat{F.col(f0), A.m, Lk - f0, A.m}, true);  // A Q_r
+  orth(c, F, Rf, f0);
   core_svd(c, Rf, Lk, W, Vj, Sv);        // R_c = U^ L V^T
   write_outputs(c, F, W, K, Vj, Lk, Sv, k, o);
 }
